@@ -1,0 +1,8 @@
+"""FP64 CPU oracle of the cut chain and reconstruction -- TEST INFRASTRUCTURE.
+
+Only the test-suite, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  The product path (the CUDA library and its binding)
+never touches it.
+"""
+from .oracle import (build, load, run, unit, philox4x32_10, unit_normals,  # noqa: F401
+                     w_pz, hadtop, real_roots, dilep_pairing, hist_bin, mass)

@@ -1,0 +1,229 @@
+"""ctypes binding of the FP64 oracle (hf_oracle.c) -- TEST INFRASTRUCTURE.
+
+Builds liboracle.so with gcc (-O2 -ffp-contract=off, no -march flags) next to
+the source on first use.  Imported only by tests, the smoke check and the
+benchmark's CPU baseline.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_CUTS = 16
+_KIND = {"njets_min": 1, "nbtag_min": 2, "lep_pt_min": 3, "met_min": 4,
+         "wnu_solvable": 5, "hadtop_chi2_max": 6, "lep_os": 7,
+         "dilep_solvable": 8, "higgs_window": 9}
+_MODEL = {"semilep": 1, "dilep": 2}
+
+
+class _Analysis(C.Structure):
+    _fields_ = [("model", C.c_int32), ("n_cuts", C.c_int32),
+                ("kind", C.c_int32 * MAX_CUTS),
+                ("param", (C.c_double * 2) * MAX_CUTS),
+                ("mW", C.c_double), ("mt", C.c_double), ("sigma_t", C.c_double),
+                ("sigma_W", C.c_double), ("mH", C.c_double),
+                ("sigma_jet", C.c_double), ("sigma_met", C.c_double),
+                ("hist_nbins", C.c_int32), ("hist_lo", C.c_double),
+                ("hist_hi", C.c_double)]
+
+
+class _UnitResult(C.Structure):
+    _fields_ = [("passed", C.c_int32), ("idx", C.c_int32 * 4),
+                ("q", C.c_double * 6)]
+
+
+class _NuSol(C.Structure):
+    _fields_ = [("nu1", C.c_double * 4), ("nu2", C.c_double * 4),
+                ("x", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (seconds).  Returns its path."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or \
+                os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + ".%d.tmp" % os.getpid()
+            subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off",
+                                   "-fno-fast-math", "-D_DEFAULT_SOURCE",
+                                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        vp = C.c_void_p
+        lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        lib.orc_unit_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, vp]
+        lib.orc_w_pz.argtypes = [vp, C.c_double, C.c_double, C.c_double, vp, vp]
+        lib.orc_w_pz.restype = C.c_int
+        lib.orc_hadtop.argtypes = [C.c_int, vp, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, vp, vp, vp, vp, vp]
+        lib.orc_hadtop.restype = C.c_double
+        lib.orc_real_roots.argtypes = [vp, C.c_int, vp]
+        lib.orc_real_roots.restype = C.c_int
+        lib.orc_dilep_pairing.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, vp, vp]
+        lib.orc_dilep_pairing.restype = C.c_int
+        lib.orc_hist_bin.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double]
+        lib.orc_hist_bin.restype = C.c_int
+        lib.orc_mass.argtypes = [vp]
+        lib.orc_mass.restype = C.c_double
+        lib.orc_unit.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp,
+                                 C.c_uint64, C.c_uint64, C.c_uint32, vp]
+        lib.orc_unit.restype = C.c_int
+        lib.orc_run.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp, C.c_uint64,
+                                C.c_uint64, C.c_uint32, vp, vp, vp, vp, vp, vp]
+        lib.orc_run.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _f32(x) -> float:
+    return float(np.float32(x))
+
+
+def _analysis(an) -> _Analysis:
+    a = _Analysis()
+    a.model = _MODEL[an["model"]]
+    cuts = an["cuts"]
+    if len(cuts) > MAX_CUTS:
+        raise ValueError("too many cuts")
+    a.n_cuts = len(cuts)
+    for i, c in enumerate(cuts):
+        a.kind[i] = _KIND[c[0]]
+        for p in range(2):
+            a.param[i][p] = _f32(c[1 + p]) if len(c) > 1 + p else 0.0
+    for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
+        setattr(a, k, _f32(an[k]))
+    nb, lo, hi = an["hist"]
+    a.hist_nbins = int(nb)
+    a.hist_lo = _f32(lo)
+    a.hist_hi = _f32(hi)
+    return a
+
+
+def _ptr(x: np.ndarray):
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def _cols(cols):
+    arrs = (np.ascontiguousarray(cols.jet_off, dtype=np.uint32),
+            np.ascontiguousarray(cols.jets, dtype=np.float32),
+            np.ascontiguousarray(cols.btag, dtype=np.uint16),
+            np.ascontiguousarray(cols.lep, dtype=np.float32),
+            np.ascontiguousarray(cols.lep_q, dtype=np.int8),
+            np.ascontiguousarray(cols.met, dtype=np.float32))
+    return arrs
+
+
+def run(an, cols, *, seed=0, V=1, first_event_id=0, unit_passed=False):
+    """Run the oracle over a whole chunk.  Returns a dict with mask (u8[N]),
+    cutflow (u64[n_cuts+1]), hist (u64[nbins+2]: under, bins, over),
+    n_surv (u16[N]), reco (f64[N,4]) and optionally unit_passed (i8[N,V])."""
+    lib = load()
+    a = _analysis(an)
+    arrs = _cols(cols)
+    N = cols.n_events
+    nb = an["hist"][0]
+    out = dict(mask=np.zeros(N, np.uint8), cutflow=np.zeros(len(an["cuts"]) + 1, np.uint64),
+               hist=np.zeros(nb + 2, np.uint64), n_surv=np.zeros(N, np.uint16),
+               reco=np.zeros((N, 4), np.float64))
+    up = np.zeros((N, V), np.int8) if unit_passed else None
+    rc = lib.orc_run(C.byref(a), N, *[_ptr(x) for x in arrs], first_event_id, seed, V,
+                     _ptr(out["mask"]), _ptr(out["cutflow"]), _ptr(out["hist"]),
+                     _ptr(out["n_surv"]), _ptr(out["reco"]),
+                     _ptr(up) if up is not None else None)
+    if rc != 0:
+        raise ValueError("oracle: invalid event columns")
+    if up is not None:
+        out["unit_passed"] = up
+    return out
+
+
+def unit(an, cols, e, v, *, seed=0, first_event_id=0):
+    """One unit (event e, variation v): dict(passed, idx[4], q[6])."""
+    lib = load()
+    a = _analysis(an)
+    arrs = _cols(cols)
+    r = _UnitResult()
+    lib.orc_unit(C.byref(a), e, *[_ptr(x) for x in arrs], first_event_id, seed, v, C.byref(r))
+    return dict(passed=r.passed, idx=list(r.idx), q=list(r.q))
+
+
+def philox4x32_10(ctr, key):
+    lib = load()
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def unit_normals(seed, event, v):
+    lib = load()
+    z = np.zeros(16, np.float64)
+    lib.orc_unit_normals(seed, event, v, _ptr(z))
+    return z
+
+
+def w_pz(lep, metx, mety, mW):
+    lib = load()
+    l4 = np.ascontiguousarray(lep, dtype=np.float64)
+    pz = C.c_double()
+    dn = C.c_int()
+    ok = lib.orc_w_pz(_ptr(l4), metx, mety, mW, C.byref(pz), C.byref(dn))
+    return bool(ok), pz.value, bool(dn.value)
+
+
+def hadtop(jets, mW, mt, sigma_W, sigma_t):
+    lib = load()
+    j = np.ascontiguousarray(jets, dtype=np.float64).reshape(-1, 4)
+    k, i, jj = C.c_int(), C.c_int(), C.c_int()
+    mtop, mw = C.c_double(), C.c_double()
+    chi2 = lib.orc_hadtop(j.shape[0], _ptr(j), mW, mt, sigma_W, sigma_t, C.byref(k),
+                          C.byref(i), C.byref(jj), C.byref(mtop), C.byref(mw))
+    return dict(chi2=chi2, k=k.value, i=i.value, j=jj.value, mtop=mtop.value, mw=mw.value)
+
+
+def real_roots(coeffs):
+    """Real roots (ascending) of sum coeffs[i] x^i, degree <= 4."""
+    lib = load()
+    c = np.zeros(5, np.float64)
+    c[:len(coeffs)] = coeffs
+    r = np.zeros(4, np.float64)
+    n = lib.orc_real_roots(_ptr(c), len(coeffs) - 1, _ptr(r))
+    return r[:n].copy()
+
+
+def dilep_pairing(l1, b1, l2, b2, metx, mety, mW, mt):
+    lib = load()
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (l1, b1, l2, b2)]
+    sol = (_NuSol * 4)()
+    quart = np.zeros(5, np.float64)
+    n = lib.orc_dilep_pairing(*[_ptr(x) for x in arrs], metx, mety, mW, mt, sol, _ptr(quart))
+    out = [dict(nu1=np.array(sol[s].nu1), nu2=np.array(sol[s].nu2), x=sol[s].x)
+           for s in range(n)]
+    return out, quart
+
+
+def hist_bin(x, nbins, lo, hi):
+    return load().orc_hist_bin(x, nbins, lo, hi)
+
+
+def mass(p4):
+    v = np.ascontiguousarray(p4, dtype=np.float64)
+    return load().orc_mass(_ptr(v))
