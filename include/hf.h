@@ -1,0 +1,219 @@
+/*
+ * hf.h -- C ABI of the GB300 event-analysis engine: an ordered cut chain
+ * with kinematic reconstruction and detector smearing, evaluated per event
+ * over millions of independent collision events on one GPU.
+ *
+ * Method: HEP-Frame (A. Pereira, A. Onofre, A. Proenca, arXiv:2211.14346).
+ *   - A user analysis is an ordered list of cuts ("propositions"); each event
+ *     is tested against them in order and stops at the first failing one; an
+ *     event passing all cuts is selected (Sect. 3, registration of cuts with
+ *     the analysis in user order; Sect. 6.1, cut example).
+ *   - Semileptonic reconstruction: neutrino p_z from the W-mass constraint
+ *     with the missing transverse momentum (MET) as the neutrino pT, and the
+ *     jet-triplet chi-square of Eq. 1 (Sect. 6.2), hadronic-top term.
+ *   - Dilepton ttH reconstruction: two neutrinos from the W-mass (80.4 GeV)
+ *     and top-mass (172.5 GeV) constraints with MET split between them, over
+ *     all b-jet/lepton pairings, the best solution kept; no solution rejects
+ *     the event; the Higgs candidate from the two remaining b-jets closest to
+ *     125 GeV (Sect. 4).
+ *   - N detector-resolution pseudo-experiments ("variations") per event
+ *     (Sect. 4), drawn from Philox4x32-10 keyed by (seed, event, variation).
+ *   - Per-cut counts (cut flow) and user histograms (Appendix).
+ *
+ * Terminology: a "unit" is one (event, variation) pair; V variations per
+ * event (V = 1 and zero widths = unsmeared).  The cut flow counts units.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HF_OK (0) or a negative hf_status.  No entry point aborts,
+ *     throws or exits; hf_last_error() gives a message for the calling thread.
+ *   - Pointers documented as "host" are CPU memory, "device" are CUDA device
+ *     memory on the context's GPU.  The library never frees caller memory.
+ *   - All entry points are thread-safe (one internal mutex per context).
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hf_status;
+#define HF_OK 0
+#define HF_EINVAL (-1)    /* invalid argument, descriptor or event columns   */
+#define HF_ENOMEM (-2)    /* device or pinned host allocation failed          */
+#define HF_EBUSY (-3)     /* admission refused: HBM budget or slots full; retry */
+#define HF_ECUDA (-4)     /* a CUDA call failed; see hf_last_error            */
+#define HF_ETIMEOUT (-5)  /* a bounded wait expired                            */
+#define HF_ENOTFOUND (-6) /* unknown ticket or analysis id                     */
+#define HF_ESTATE (-7)    /* call not valid in the current state               */
+
+typedef struct hf_ctx hf_ctx;
+
+/* hf_config.flags */
+#define HF_FLAG_PLAIN 1u      /* run every chunk with the plain one-thread-per-event kernel */
+#define HF_FLAG_NO_SCHED 2u   /* keep the user order for execution (no reordering)         */
+#define HF_FLAG_DEBUG_SYNC 4u /* synchronise after every launch and check errors           */
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal                                   */
+    uint32_t flags;            /* HF_FLAG_*                                             */
+    uint64_t hbm_budget_bytes; /* admission budget for in-flight chunks (0 = 80% of free) */
+    uint32_t max_inflight;     /* maximum in-flight tickets (0 = 64)                    */
+    uint32_t reserved;
+    void* stream;              /* optional cudaStream_t to order work after (NULL = own) */
+} hf_config;
+
+/* Opens a context on cfg->device.  cfg may be NULL (device 0, defaults).
+ * *out receives the context; release it with hf_close.
+ * Errors: HF_EINVAL (bad device), HF_ECUDA, HF_ENOMEM. */
+hf_status hf_open(const hf_config* cfg, hf_ctx** out);
+
+/* Closes the context: waits (bounded, 60 s) for in-flight work, frees all
+ * device and pinned memory it owns.  ctx may be NULL.  Returns HF_ETIMEOUT if
+ * work did not finish in time (memory is then leaked, not freed under a
+ * running kernel). */
+hf_status hf_close(hf_ctx* ctx);
+
+/* Message of the last error on the calling thread (static storage, never NULL). */
+const char* hf_last_error(hf_ctx* ctx);
+
+/* ------------------------------------------------------------------ */
+/* Analysis description (hf_define_cuts).                               */
+/* ------------------------------------------------------------------ */
+#define HF_MODEL_SEMILEP 1 /* one lepton; needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX */
+#define HF_MODEL_DILEP 2   /* two leptons; needs HF_CUT_DILEP_SOLVABLE and HF_CUT_HIGGS_WINDOW   */
+
+/* Cut kinds.  Each is a pure predicate of one unit, so any user order gives
+ * the same selected units (only the cut flow, reported in user order, changes). */
+#define HF_CUT_NJETS_MIN 1       /* n_jets >= params[0]                                    */
+#define HF_CUT_NBTAG_MIN 2       /* b-tagged jets >= params[0]                             */
+#define HF_CUT_LEP_PT_MIN 3      /* pT(lepton 1) > params[0] GeV                           */
+#define HF_CUT_MET_MIN 4         /* |MET| > params[0] GeV, after smearing                  */
+#define HF_CUT_W_NU_SOLVABLE 5   /* W-mass neutrino p_z exists (Sect. 6.2)                 */
+#define HF_CUT_HADTOP_CHI2_MAX 6 /* min over jet triplets of Eq. 1 hadronic chi2 < params[0] */
+#define HF_CUT_LEP_OS 7          /* q1 * q2 < 0                                            */
+#define HF_CUT_DILEP_SOLVABLE 8  /* >= 1 two-neutrino solution over b-jet pairings (Sect. 4) */
+#define HF_CUT_HIGGS_WINDOW 9    /* params[0] < m_bb < params[1] (Sect. 4)                  */
+
+typedef struct {
+    int32_t kind;      /* HF_CUT_*                                                     */
+    float params[4];   /* thresholds; integers for counts                              */
+    uint32_t dep_mask; /* bit j: this cut must execute after user-order cut j           */
+    uint8_t reorderable; /* 0 pins this cut to its user position for execution        */
+    uint8_t pad[3];
+} hf_cut;
+
+typedef struct {
+    int32_t event_model; /* HF_MODEL_*                                              */
+    uint32_t n_cuts;     /* 1..16                                                    */
+    const hf_cut* cuts;  /* host, n_cuts entries, USER order; copied by the call      */
+    float mW, mt;        /* W and top masses, GeV (Sect. 4: 80.4, 172.5)              */
+    float sigma_t, sigma_W; /* widths of Eq. 1, GeV                                  */
+    float mH;            /* Higgs mass for the b-jet pair, GeV (Sect. 4: 125)          */
+    float sigma_jet;     /* relative jet-energy resolution of the smearing, [0, 0.15]  */
+    float sigma_met;     /* absolute MET resolution per component, GeV, >= 0           */
+    uint32_t hist_nbins; /* reconstructed-mass histogram: bins, 1..4096                */
+    float hist_lo, hist_hi; /* range, GeV; hist_lo < hist_hi                            */
+} hf_analysis_desc;
+
+/* Validates and registers an analysis.  *analysis_id receives its id.
+ * Errors: HF_EINVAL (unknown kind, n_cuts out of range, missing
+ * reconstruction cut for the model, dependency cycle, bad widths/histogram). */
+hf_status hf_define_cuts(hf_ctx* ctx, const hf_analysis_desc* desc, uint32_t* analysis_id);
+
+/* ------------------------------------------------------------------ */
+/* Event columns (structure of arrays, one chunk of N events).          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const uint32_t* jet_off; /* N+1 offsets into jets; jet_off[0] = 0; n_jets <= 12   */
+    const float* jets;       /* 4*J floats: (px, py, pz, E) per jet, GeV, 16-byte aligned */
+    const uint16_t* btag;    /* N: bit i <=> jet i of the event is b-tagged          */
+    const float* lep;        /* 4*L*N floats: (px, py, pz, E) of L leptons per event  */
+    const int8_t* lep_q;     /* L*N charges                                         */
+    const float* met;        /* 2*N floats: MET (x, y), GeV                           */
+    uint64_t n_jets_total;   /* J = jet_off[N]                                       */
+} hf_columns;
+
+/* Results; every pointer may be NULL to skip that field. */
+typedef struct {
+    uint8_t* mask;      /* N: 1 if at least one variation of the event passed every cut */
+    uint64_t* cutflow;  /* n_cuts+1, user order: [0] = units in, [k] = units passing cuts 1..k */
+    uint64_t* hist;     /* hist_nbins+2: [0] underflow, [1..nbins] bins, [nbins+1] overflow  */
+    uint16_t* n_surv;   /* N: variations of the event passing every cut                  */
+    float* reco;        /* 4*N: per-event mean over passing variations, summed in variation
+                           order; semileptonic (m_top, m_W, pz_nu, |MET|), dilepton
+                           (m_bb, m_t, m_tbar, m_ttbar); zeros when n_surv = 0           */
+    uint64_t* recheck_count; /* 1: units re-evaluated in FP64 (diagnostic)              */
+} hf_results;
+
+/* Asynchronous chunk submission.  host_cols are HOST pointers, caller-owned,
+ * that must stay valid and unchanged until the ticket is DONE or FAILED
+ * (the library copies them to the device, from pinned memory directly or via
+ * its pinned staging).  first_event_id is the global id of event 0 (it keys
+ * the smearing); seed keys the smearing; n_variations = V >= 1.
+ * *ticket receives the ticket.  Errors: HF_EINVAL (bad columns or sizes),
+ * HF_ENOTFOUND (analysis), HF_EBUSY (budget or slots; nothing enqueued),
+ * HF_ENOMEM, HF_ECUDA.  Malformed offsets or n_jets > 12 found on the device
+ * make the ticket FAILED with HF_EINVAL at fetch. */
+hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* host_cols,
+                          uint64_t n_events, uint64_t first_event_id, uint64_t seed,
+                          uint32_t n_variations, uint64_t* ticket);
+
+#define HF_STATE_QUEUED 0
+#define HF_STATE_RUNNING 1
+#define HF_STATE_DONE 2
+#define HF_STATE_FAILED 3
+
+/* Non-blocking state query of a ticket.  Errors: HF_ENOTFOUND. */
+hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state);
+
+/* Waits (bounded by timeout_ms; 0 = poll once) for the ticket, then copies its
+ * results into the caller's HOST buffers of `out` (NULL fields skipped) and
+ * releases the ticket.  Errors: HF_ETIMEOUT (ticket kept), HF_ENOTFOUND,
+ * HF_EINVAL (device found malformed columns; ticket released), HF_ECUDA. */
+hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32_t timeout_ms);
+
+/* Synchronous-on-stream run over DEVICE-resident columns: enqueues the whole
+ * path on `stream` (cudaStream_t, NULL = the context's stream) and writes the
+ * results into DEVICE buffers of `dev_out` (NULL fields skipped; cutflow and
+ * hist are overwritten, not accumulated).  Scratch memory is owned by the
+ * context and reused; calls on one context are serialised by its mutex, and
+ * results are valid once the stream reaches them.  n_events may be 0.
+ * Errors: HF_EINVAL, HF_ENOTFOUND, HF_ENOMEM, HF_ECUDA.  Malformed columns set
+ * the error word readable with hf_device_error. */
+hf_status hf_run_device(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols,
+                        uint64_t n_events, uint64_t first_event_id, uint64_t seed,
+                        uint32_t n_variations, const hf_results* dev_out, void* stream);
+
+/* Same as hf_run_device with the plain form: one thread per event, cuts in user
+ * order, jets read from global memory, no compaction, staging or reordering.
+ * Identical results (same FP32 bands and FP64 recheck); the comparison baseline. */
+hf_status hf_run_device_plain(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols,
+                              uint64_t n_events, uint64_t first_event_id, uint64_t seed,
+                              uint32_t n_variations, const hf_results* dev_out, void* stream);
+
+/* Waits for the context's stream and returns the device error word of the
+ * last hf_run_device* call in *word (0 = none; bit 0 = malformed offsets or
+ * n_jets > 12).  Errors: HF_ECUDA. */
+hf_status hf_device_error(hf_ctx* ctx, uint32_t* word);
+
+/* Scheduler state of an analysis: current execution order of its cuts
+ * (user indices, n_cuts entries) and per-cut statistics accumulated so far
+ * (units evaluated, units passed, summed cost in SM cycles).  Any pointer may
+ * be NULL.  Synchronises the context's stream.  Errors: HF_ENOTFOUND. */
+hf_status hf_sched_state(hf_ctx* ctx, uint32_t analysis_id, int32_t* exec_order,
+                         uint64_t* evaluated, uint64_t* passed, uint64_t* cost);
+
+/* Forces the execution order of an analysis's cuts (user indices); it must
+ * respect dependencies.  Disables automatic reordering for that analysis.
+ * Used to check that results do not depend on execution order.
+ * Errors: HF_EINVAL (not a valid dependency-respecting permutation). */
+hf_status hf_set_exec_order(hf_ctx* ctx, uint32_t analysis_id, const int32_t* exec_order);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

@@ -758,14 +758,16 @@ int orc_unit(const orc_analysis* an, uint64_t e, const uint32_t* jet_off, const 
  * m_bb dilepton) and adds its reconstructed quantities, in variation order,
  * to the event's sums; reco[e] = sums / n_surv[e], mask[e] = n_surv[e] >= 1.
  * reco per event (4 values): semilep (m_top, m_W, pz_nu, |MET'|), dilep
- * (m_bb, m_t, m_tbar, m_ttbar); all zero when no unit survives.
+ * (m_bb, m_t, m_tbar, m_ttbar); all zero when no unit survives.  reco_abs
+ * (optional) receives the means of the absolute values, the magnitude scale
+ * of a signed mean such as p_z.
  * Returns 0, or -1 for an invalid event (more than 12 jets).
  */
 int orc_run(const orc_analysis* an, uint64_t N, const uint32_t* jet_off, const float* jets,
             const uint16_t* btag, const float* lep, const int8_t* lep_q, const float* met,
             uint64_t first_event_id, uint64_t seed, uint32_t V, uint8_t* mask,
             uint64_t* cutflow, uint64_t* hist, uint16_t* n_surv, double* reco,
-            int8_t* unit_passed)
+            int8_t* unit_passed, double* reco_abs)
 {
     for (int c = 0; c <= an->n_cuts; ++c)
         cutflow[c] = 0;
@@ -776,7 +778,7 @@ int orc_run(const orc_analysis* an, uint64_t N, const uint32_t* jet_off, const f
             return -1;
         orc_event ev;
         load_event(an, e, jet_off, jets, btag, lep, lep_q, met, &ev);
-        double sum[4] = {0.0, 0.0, 0.0, 0.0};
+        double sum[4] = {0.0, 0.0, 0.0, 0.0}, sabs[4] = {0.0, 0.0, 0.0, 0.0};
         int ns = 0;
         for (uint32_t v = 0; v < V; ++v) {
             orc_unit_result r;
@@ -789,14 +791,19 @@ int orc_run(const orc_analysis* an, uint64_t N, const uint32_t* jet_off, const f
                 ++ns;
                 double x = r.q[0];
                 hist[orc_hist_bin(x, an->hist_nbins, an->hist_lo, an->hist_hi)] += 1;
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < 4; ++k) {
                     sum[k] = sum[k] + r.q[k];
+                    sabs[k] = sabs[k] + fabs(r.q[k]);
+                }
             }
         }
         n_surv[e] = (uint16_t)ns;
         mask[e] = ns >= 1;
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k) {
             reco[4 * e + k] = ns ? sum[k] / (double)ns : 0.0;
+            if (reco_abs)
+                reco_abs[4 * e + k] = ns ? sabs[k] / (double)ns : 0.0;
+        }
     }
     return 0;
 }

@@ -86,7 +86,7 @@ def load():
                                  C.c_uint64, C.c_uint64, C.c_uint32, vp]
         lib.orc_unit.restype = C.c_int
         lib.orc_run.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp, C.c_uint64,
-                                C.c_uint64, C.c_uint32, vp, vp, vp, vp, vp, vp]
+                                C.c_uint64, C.c_uint32, vp, vp, vp, vp, vp, vp, vp]
         lib.orc_run.restype = C.c_int
         _lib = lib
     return _lib
@@ -133,7 +133,8 @@ def _cols(cols):
 def run(an, cols, *, seed=0, V=1, first_event_id=0, unit_passed=False):
     """Run the oracle over a whole chunk.  Returns a dict with mask (u8[N]),
     cutflow (u64[n_cuts+1]), hist (u64[nbins+2]: under, bins, over),
-    n_surv (u16[N]), reco (f64[N,4]) and optionally unit_passed (i8[N,V])."""
+    n_surv (u16[N]), reco (f64[N,4]), reco_abs (f64[N,4], means of |value|)
+    and optionally unit_passed (i8[N,V])."""
     lib = load()
     a = _analysis(an)
     arrs = _cols(cols)
@@ -141,12 +142,12 @@ def run(an, cols, *, seed=0, V=1, first_event_id=0, unit_passed=False):
     nb = an["hist"][0]
     out = dict(mask=np.zeros(N, np.uint8), cutflow=np.zeros(len(an["cuts"]) + 1, np.uint64),
                hist=np.zeros(nb + 2, np.uint64), n_surv=np.zeros(N, np.uint16),
-               reco=np.zeros((N, 4), np.float64))
+               reco=np.zeros((N, 4), np.float64), reco_abs=np.zeros((N, 4), np.float64))
     up = np.zeros((N, V), np.int8) if unit_passed else None
     rc = lib.orc_run(C.byref(a), N, *[_ptr(x) for x in arrs], first_event_id, seed, V,
                      _ptr(out["mask"]), _ptr(out["cutflow"]), _ptr(out["hist"]),
                      _ptr(out["n_surv"]), _ptr(out["reco"]),
-                     _ptr(up) if up is not None else None)
+                     _ptr(up) if up is not None else None, _ptr(out["reco_abs"]))
     if rc != 0:
         raise ValueError("oracle: invalid event columns")
     if up is not None:

@@ -1,0 +1,256 @@
+"""GB300 engine for HEP-Frame-style event analysis (arXiv:2211.14346): an
+ordered cut chain with kinematic reconstruction and detector smearing,
+evaluated per event on one GPU behind the C ABI of include/hf.h.
+
+This package is the thin Python side: `_lib` marshals arguments to the C
+entry points of the same names, `Engine` wraps a context and converts the
+user-level analysis description and numpy / torch columns.  PyTorch is used
+only to hold device and pinned host buffers; all computation runs in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HFError,  # noqa: F401
+                   HF_STATE_DONE, HF_STATE_FAILED, HF_STATE_QUEUED, HF_STATE_RUNNING)
+
+N_RECO = 4
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the handle of the legacy default stream
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def _cut_struct(cuts):
+    arr = (_lib.hf_cut * len(cuts))()
+    for i, c in enumerate(cuts):
+        name, params = c[0], list(c[1:])
+        deps, reorder = 0, 1
+        if params and isinstance(params[-1], dict):
+            opt = params.pop()
+            deps = int(opt.get("dep_mask", 0))
+            reorder = int(opt.get("reorderable", 1))
+        arr[i].kind = _lib.HF_CUT[name]
+        for k, p in enumerate(params[:4]):
+            arr[i].params[k] = _f32(p)
+        arr[i].dep_mask = deps
+        arr[i].reorderable = reorder
+    return arr
+
+
+def columns_struct(ptrs, n_jets_total):
+    """hf_columns from raw addresses (host or device)."""
+    s = _lib.hf_columns()
+    s.jet_off, s.jets, s.btag, s.lep, s.lep_q, s.met = ptrs
+    s.n_jets_total = int(n_jets_total)
+    return s
+
+
+class DeviceColumns:
+    """A chunk's columns as torch CUDA tensors (device memory only)."""
+
+    def __init__(self, cols, device="cuda"):
+        import torch
+        self.model = cols.model
+        self.n_events = cols.n_events
+        self.n_jets_total = cols.n_jets_total
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+        self.jet_off = t(cols.jet_off.view(np.int32))
+        self.jets = t(cols.jets)
+        self.btag = t(cols.btag.view(np.int16))
+        self.lep = t(cols.lep)
+        self.lep_q = t(cols.lep_q)
+        self.met = t(cols.met)
+
+    def struct(self):
+        return columns_struct([x.data_ptr() for x in (self.jet_off, self.jets, self.btag, self.lep,
+                                                       self.lep_q, self.met)], self.n_jets_total)
+
+    def nbytes(self):
+        return sum(x.numel() * x.element_size() for x in (self.jet_off, self.jets, self.btag, self.lep,
+                                                           self.lep_q, self.met))
+
+
+class PinnedColumns:
+    """A chunk's columns in pinned (page-locked) host memory."""
+
+    def __init__(self, cols):
+        import torch
+        self.model = cols.model
+        self.n_events = cols.n_events
+        self.n_jets_total = cols.n_jets_total
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        self.jet_off = t(cols.jet_off.view(np.int32))
+        self.jets = t(cols.jets)
+        self.btag = t(cols.btag.view(np.int16))
+        self.lep = t(cols.lep)
+        self.lep_q = t(cols.lep_q)
+        self.met = t(cols.met)
+
+    def struct(self):
+        return columns_struct([x.data_ptr() for x in (self.jet_off, self.jets, self.btag, self.lep,
+                                                       self.lep_q, self.met)], self.n_jets_total)
+
+    def nbytes(self):
+        return sum(x.numel() * x.element_size() for x in (self.jet_off, self.jets, self.btag, self.lep,
+                                                           self.lep_q, self.met))
+
+
+class HostColumnsView:
+    """hf_columns over numpy arrays (pageable host memory)."""
+
+    def __init__(self, cols):
+        self._keep = [np.ascontiguousarray(a) for a in (cols.jet_off, cols.jets, cols.btag, cols.lep,
+                                                        cols.lep_q, cols.met)]
+        self.n_events = cols.n_events
+        self.n_jets_total = cols.n_jets_total
+
+    def struct(self):
+        return columns_struct([a.ctypes.data for a in self._keep], self.n_jets_total)
+
+
+class DeviceResults:
+    """Device result buffers of one run (torch CUDA tensors)."""
+
+    def __init__(self, n_events, n_cuts, nbins, device="cuda"):
+        import torch
+        self.mask = torch.zeros(n_events, dtype=torch.uint8, device=device)
+        self.cutflow = torch.zeros(n_cuts + 1, dtype=torch.int64, device=device)
+        self.hist = torch.zeros(nbins + 2, dtype=torch.int64, device=device)
+        self.n_surv = torch.zeros(n_events, dtype=torch.int16, device=device)
+        self.reco = torch.zeros((n_events, N_RECO), dtype=torch.float32, device=device)
+        self.recheck_count = torch.zeros(1, dtype=torch.int64, device=device)
+
+    def struct(self, fields=None):
+        s = _lib.hf_results()
+        for f in ("mask", "cutflow", "hist", "n_surv", "reco", "recheck_count"):
+            if fields is None or f in fields:
+                setattr(s, f, getattr(self, f).data_ptr())
+        return s
+
+    def numpy(self):
+        return dict(mask=self.mask.cpu().numpy(), cutflow=self.cutflow.cpu().numpy().astype(np.uint64),
+                    hist=self.hist.cpu().numpy().astype(np.uint64),
+                    n_surv=self.n_surv.cpu().numpy().view(np.uint16), reco=self.reco.cpu().numpy(),
+                    recheck_count=int(self.recheck_count.cpu().item()))
+
+
+class Engine:
+    """One library context on one GPU."""
+
+    def __init__(self, device=0, flags=0, hbm_budget_bytes=0, max_inflight=0):
+        self.lib = _lib.load()
+        cfg = _lib.hf_config(device, flags, hbm_budget_bytes, max_inflight, 0, None)
+        ctx = C.c_void_p()
+        _lib.check(self.lib.hf_open(C.byref(cfg), C.byref(ctx)))
+        self.ctx = ctx
+        self._analyses = {}
+
+    def close(self):
+        if self.ctx is not None:
+            _lib.check(self.lib.hf_close(self.ctx))
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        return _lib.check(st, self.ctx)
+
+    def define(self, an) -> int:
+        """Registers a user-level analysis (see synth.analyses).  Returns its id."""
+        cuts = _cut_struct(an["cuts"])
+        d = _lib.hf_analysis_desc()
+        d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
+        d.n_cuts = len(an["cuts"])
+        d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
+        for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
+            setattr(d, k, _f32(an[k]))
+        nb, lo, hi = an["hist"]
+        d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
+        aid = C.c_uint32()
+        self._check(self.lib.hf_define_cuts(self.ctx, C.byref(d), C.byref(aid)))
+        self._analyses[aid.value] = an
+        return aid.value
+
+    def results_for(self, aid, n_events, device="cuda"):
+        an = self._analyses[aid]
+        return DeviceResults(n_events, len(an["cuts"]), an["hist"][0], device)
+
+    def run_device(self, aid, dcols, *, V=1, seed=0, first_event_id=0, out=None, plain=False, stream=None,
+                   fields=None):
+        """Runs the whole path on device-resident columns; returns DeviceResults."""
+        if out is None:
+            out = self.results_for(aid, dcols.n_events)
+        if stream is None:
+            # order the run after torch's uploads and before its reads
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+        cs = dcols.struct()
+        rs = out.struct(fields)
+        fn = self.lib.hf_run_device_plain if plain else self.lib.hf_run_device
+        self._check(fn(self.ctx, aid, C.byref(cs), dcols.n_events, first_event_id, seed, V, C.byref(rs),
+                       stream))
+        return out
+
+    def device_error(self):
+        w = C.c_uint32()
+        self._check(self.lib.hf_device_error(self.ctx, C.byref(w)))
+        return w.value
+
+    def submit(self, aid, hcols, *, V=1, seed=0, first_event_id=0):
+        """Submits host columns (PinnedColumns or HostColumnsView); returns a ticket."""
+        cs = hcols.struct()
+        t = C.c_uint64()
+        self._check(self.lib.hf_submit_chunk(self.ctx, aid, C.byref(cs), hcols.n_events, first_event_id, seed,
+                                             V, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        s = C.c_int32()
+        self._check(self.lib.hf_poll(self.ctx, ticket, C.byref(s)))
+        return s.value
+
+    def fetch(self, aid, ticket, n_events, *, fields=("mask", "cutflow", "hist", "n_surv", "reco",
+                                                        "recheck_count"), timeout_ms=600000, out=None):
+        """Waits for a ticket and copies its results to host numpy arrays."""
+        an = self._analyses[aid]
+        if out is None:
+            out = {}
+            if "mask" in fields:
+                out["mask"] = np.zeros(n_events, np.uint8)
+            if "cutflow" in fields:
+                out["cutflow"] = np.zeros(len(an["cuts"]) + 1, np.uint64)
+            if "hist" in fields:
+                out["hist"] = np.zeros(an["hist"][0] + 2, np.uint64)
+            if "n_surv" in fields:
+                out["n_surv"] = np.zeros(n_events, np.uint16)
+            if "reco" in fields:
+                out["reco"] = np.zeros((n_events, N_RECO), np.float32)
+            if "recheck_count" in fields:
+                out["recheck_count"] = np.zeros(1, np.uint64)
+        rs = _lib.hf_results()
+        for f, a in out.items():
+            setattr(rs, f, a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+        self._check(self.lib.hf_fetch_results(self.ctx, ticket, C.byref(rs), timeout_ms))
+        return out
+
+    def sched_state(self, aid):
+        n = len(self._analyses[aid]["cuts"])
+        order = np.zeros(n, np.int32)
+        ev, ps, co = (np.zeros(n, np.uint64) for _ in range(3))
+        self._check(self.lib.hf_sched_state(self.ctx, aid, order.ctypes.data, ev.ctypes.data, ps.ctypes.data,
+                                            co.ctypes.data))
+        return dict(order=order, evaluated=ev, passed=ps, cost=co)
+
+    def set_exec_order(self, aid, order):
+        o = np.ascontiguousarray(order, dtype=np.int32)
+        self._check(self.lib.hf_set_exec_order(self.ctx, aid, o.ctypes.data))

@@ -1,0 +1,777 @@
+// hf_api.cpp -- host runtime behind the C ABI declared in include/hf.h.
+//
+// One context per GPU.  A context owns three CUDA streams (host-to-device
+// copies, compute, device-to-host copies), the registered analyses with
+// their device-side scheduler state, a scratch arena for runs over
+// device-resident columns, and the table of asynchronous tickets.  Device
+// memory of tickets comes from the stream-ordered allocator
+// (cudaMallocAsync), so that admission, copies, kernels and release of many
+// in-flight chunks overlap without host synchronisation.
+#include "hf.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hf_dev.cuh"
+#include "hf_kernels.h"
+#include "hf_sched.h"
+
+using namespace hf;
+
+namespace {
+
+thread_local std::string g_err = "";
+
+hf_status fail(hf_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+hf_status cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return HF_ECUDA;
+}
+
+#define HF_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Analysis {
+    Plan plan;
+    std::vector<hf_cut> cuts;
+    SchedDev* sched = nullptr;  // device
+    bool no_sched = false;
+};
+
+// Layout of the device memory of one run (scratch + optional columns +
+// optional results), carved from one allocation.
+struct RunLayout {
+    size_t off_small = 0, off_bucket = 0, off_rc = 0, off_pend_cnt = 0, off_pend_left = 0, off_pend_sum = 0,
+           off_pend_comp = 0, off_stats = 0, off_cutflow = 0, off_hist = 0, off_rctot = 0;
+    size_t scratch_bytes = 0;
+    unsigned rc_cap = 0;
+};
+
+RunLayout layout_for(uint64_t N, uint32_t V)
+{
+    RunLayout L;
+    size_t o = 0;
+    L.off_small = o;
+    o += 256;
+    L.off_bucket = o = align_up(o, 256);
+    o += sizeof(uint2) * std::max<uint64_t>(N, 1);
+    uint64_t units = N * (uint64_t)V;
+    uint64_t cap = std::max<uint64_t>(65536, units / 64);
+    cap = std::min<uint64_t>(cap, 1u << 30);
+    L.rc_cap = (unsigned)cap;
+    L.off_rc = o = align_up(o, 256);
+    o += sizeof(RcEntry) * cap;
+    L.off_pend_cnt = o = align_up(o, 256);
+    o += 4 * cap;
+    L.off_pend_left = o = align_up(o, 256);
+    o += 4 * cap;
+    L.off_pend_sum = o = align_up(o, 256);
+    o += 16 * cap;
+    L.off_pend_comp = o = align_up(o, 256);
+    o += 16 * cap;
+    L.off_stats = o = align_up(o, 256);
+    o += 8 * 3 * MAX_CUTS;
+    L.off_cutflow = o = align_up(o, 256);
+    o += 8 * (MAX_CUTS + 1);
+    L.off_hist = o = align_up(o, 256);
+    o += 8 * (MAX_BINS + 2);
+    L.off_rctot = o = align_up(o, 256);
+    o += 8;
+    L.scratch_bytes = align_up(o, 256);
+    return L;
+}
+
+// Offsets inside the "small" block: counters zeroed per run.
+constexpr size_t SM_NHIST = 0, SM_CURSOR = 64, SM_TILE = 128, SM_RC = 192, SM_RCVALID = 196, SM_PEND = 200,
+                 SM_ERR = 204;
+
+Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
+{
+    Scratch S;
+    char* sm = base + L.off_small;
+    S.nhist = (unsigned*)(sm + SM_NHIST);
+    S.cursor = (unsigned*)(sm + SM_CURSOR);
+    S.tile_ctr = (unsigned*)(sm + SM_TILE);
+    S.rc_count = (unsigned*)(sm + SM_RC);
+    S.rc_valid = (unsigned*)(sm + SM_RCVALID);
+    S.pend_count = (unsigned*)(sm + SM_PEND);
+    S.err = (unsigned*)(sm + SM_ERR);
+    S.bucket = (uint2*)(base + L.off_bucket);
+    S.rc = (RcEntry*)(base + L.off_rc);
+    S.rc_cap = L.rc_cap;
+    S.pend_cnt = (unsigned*)(base + L.off_pend_cnt);
+    S.pend_left = (unsigned*)(base + L.off_pend_left);
+    S.pend_sum = (float4*)(base + L.off_pend_sum);
+    S.pend_comp = (float4*)(base + L.off_pend_comp);
+    S.stats = (unsigned long long*)(base + L.off_stats);
+    S.exec2 = A.sched ? A.sched->exec2 : nullptr;
+    S.n_exec2 = A.plan.n_exec2;
+    return S;
+}
+
+// Bytes of the device columns of N events with J jets.
+struct ColLayout {
+    size_t off_jet_off, off_jets, off_btag, off_lep, off_lep_q, off_met, bytes;
+};
+ColLayout col_layout(uint64_t N, uint64_t J, int L)
+{
+    ColLayout c;
+    size_t o = 0;
+    c.off_jets = o;
+    o += 16 * J;
+    c.off_lep = o = align_up(o, 256);
+    o += 16 * (uint64_t)L * N;
+    c.off_met = o = align_up(o, 256);
+    o += 8 * N;
+    c.off_jet_off = o = align_up(o, 256);
+    o += 4 * (N + 1);
+    c.off_btag = o = align_up(o, 256);
+    o += 2 * N;
+    c.off_lep_q = o = align_up(o, 256);
+    o += (uint64_t)L * N;
+    c.bytes = align_up(o, 256);
+    return c;
+}
+
+struct ResLayout {
+    size_t off_mask, off_nsurv, off_reco, bytes;
+};
+ResLayout res_layout(uint64_t N)
+{
+    ResLayout r;
+    size_t o = 0;
+    r.off_reco = o;
+    o += 16 * N;
+    r.off_nsurv = o = align_up(o, 256);
+    o += 2 * N;
+    r.off_mask = o = align_up(o, 256);
+    o += N;
+    r.bytes = align_up(o, 256);
+    return r;
+}
+
+struct Ticket {
+    uint64_t id = 0;
+    uint32_t analysis = 0;
+    uint64_t N = 0;
+    char* dmem = nullptr;  // one stream-ordered allocation
+    size_t bytes = 0;
+    RunLayout L;
+    ResLayout R;
+    cudaEvent_t done = nullptr;
+    bool failed_launch = false;
+};
+
+}  // namespace
+
+struct hf_ctx {
+    int device = 0;
+    int sms = 0;
+    uint32_t flags = 0;
+    uint64_t budget = 0;
+    uint32_t max_inflight = 64;
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    cudaStream_t user_stream = nullptr;
+    std::mutex mu;
+    std::vector<std::unique_ptr<Analysis>> analyses;
+    // scratch arena for device-resident runs
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    cudaEvent_t arena_free = nullptr;  // last run that used the arena
+    // tickets
+    std::map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    uint64_t inflight_bytes = 0;
+};
+
+namespace {
+
+// Chooses the device for the calling thread.
+hf_status use_device(hf_ctx* ctx)
+{
+    HF_CUDA(cudaSetDevice(ctx->device));
+    return HF_OK;
+}
+
+bool known_kind(int k) { return k >= CUT_NJETS_MIN && k <= CUT_HIGGS_WINDOW; }
+
+hf_status build_plan(const hf_analysis_desc* d, Analysis& A)
+{
+    if (!d) return fail(HF_EINVAL, "desc is NULL");
+    if (d->event_model != MODEL_SEMILEP && d->event_model != MODEL_DILEP)
+        return fail(HF_EINVAL, "unknown event model");
+    if (d->event_model == MODEL_DILEP) return fail(HF_EINVAL, "dilepton model not available in this build");
+    if (d->n_cuts < 1 || d->n_cuts > (uint32_t)MAX_CUTS || !d->cuts) return fail(HF_EINVAL, "n_cuts must be 1..16");
+    if (!(d->sigma_t > 0) || !(d->sigma_W > 0)) return fail(HF_EINVAL, "widths must be > 0");
+    if (!(d->sigma_jet >= 0.0f && d->sigma_jet <= 0.15f))
+        return fail(HF_EINVAL, "sigma_jet must be in [0, 0.15] (jet scale factors stay positive)");
+    if (!(d->sigma_met >= 0.0f) || !std::isfinite(d->sigma_met)) return fail(HF_EINVAL, "sigma_met must be >= 0");
+    if (d->hist_nbins < 1 || d->hist_nbins > (uint32_t)MAX_BINS || !(d->hist_lo < d->hist_hi))
+        return fail(HF_EINVAL, "histogram: 1..1024 bins and lo < hi");
+    Plan& P = A.plan;
+    memset(&P, 0, sizeof P);
+    P.model = d->event_model;
+    P.n_cuts = (int)d->n_cuts;
+    bool have_top = false, have_w = false, have_dl = false, have_h = false;
+    A.cuts.assign(d->cuts, d->cuts + d->n_cuts);
+    for (int c = 0; c < P.n_cuts; ++c) {
+        const hf_cut& cut = d->cuts[c];
+        if (!known_kind(cut.kind)) return fail(HF_EINVAL, "unknown cut kind");
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(cut.params[k])) return fail(HF_EINVAL, "non-finite cut parameter");
+        if (cut.dep_mask >> c) return fail(HF_EINVAL, "a cut may depend only on earlier user-order cuts");
+        bool semi_only = cut.kind == CUT_W_NU_SOLVABLE || cut.kind == CUT_HADTOP_CHI2_MAX;
+        bool dl_only = cut.kind == CUT_LEP_OS || cut.kind == CUT_DILEP_SOLVABLE || cut.kind == CUT_HIGGS_WINDOW;
+        if (semi_only && P.model != MODEL_SEMILEP) return fail(HF_EINVAL, "semileptonic cut in a dilepton analysis");
+        if (dl_only && P.model != MODEL_DILEP) return fail(HF_EINVAL, "dilepton cut in a semileptonic analysis");
+        P.kind[c] = cut.kind;
+        P.p0[c] = cut.params[0];
+        P.p1[c] = cut.params[1];
+        P.dp0[c] = cut.params[0];
+        P.dp1[c] = cut.params[1];
+        have_top |= cut.kind == CUT_HADTOP_CHI2_MAX;
+        have_w |= cut.kind == CUT_W_NU_SOLVABLE;
+        have_dl |= cut.kind == CUT_DILEP_SOLVABLE;
+        have_h |= cut.kind == CUT_HIGGS_WINDOW;
+    }
+    if (P.model == MODEL_SEMILEP && !(have_top && have_w))
+        return fail(HF_EINVAL, "semileptonic analysis needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX");
+    if (P.model == MODEL_DILEP && !(have_dl && have_h))
+        return fail(HF_EINVAL, "dilepton analysis needs HF_CUT_DILEP_SOLVABLE and HF_CUT_HIGGS_WINDOW");
+    P.mW = d->mW;
+    P.mt = d->mt;
+    P.sigma_t = d->sigma_t;
+    P.sigma_W = d->sigma_W;
+    P.inv_sigma_t = 1.0f / d->sigma_t;
+    P.inv_sigma_W = 1.0f / d->sigma_W;
+    P.mH = d->mH;
+    {
+        double h = (double)d->mW * (double)d->mW / 2.0;  // exact: 24-bit factors
+        P.mW2half = (float)h;
+        P.mW2half_lo = (float)(h - (double)P.mW2half);
+    }
+    P.sigma_jet = d->sigma_jet;
+    P.sigma_met = d->sigma_met;
+    P.smear_jets = d->sigma_jet != 0.0f;
+    P.smear_met = d->sigma_met != 0.0f;
+    P.nbins = (int)d->hist_nbins;
+    P.lo = d->hist_lo;
+    P.hi = d->hist_hi;
+    P.w = (float)(((double)d->hist_hi - (double)d->hist_lo) / d->hist_nbins);
+    P.dmW = d->mW;
+    P.dmt = d->mt;
+    P.dsigma_t = d->sigma_t;
+    P.dsigma_W = d->sigma_W;
+    P.dmH = d->mH;
+    P.dsigma_jet = d->sigma_jet;
+    P.dsigma_met = d->sigma_met;
+    P.dlo = d->hist_lo;
+    P.dhi = d->hist_hi;
+    // FP32 error model: normals within 2.5 ulp (bound 4e-7 relative), |z| <= 5.8;
+    // jet scale s = 1 + sigma z within sigma * 4e-7 * 5.8 / (1 - 5.8 sigma) + 2^-24
+    // relative; a Gram-matrix mass squared within 2 s_rel + 12 u, the mass within half of
+    // that plus 3 ulp (rsqrtf and the product).
+    const double u = 5.9604644775390625e-08;
+    P.z_rel = 4.0e-7f;
+    double zmax = 5.8;
+    double s_rel = (double)d->sigma_jet * 4.0e-7 * zmax / (1.0 - zmax * (double)d->sigma_jet) + u;
+    P.s_rel = (float)s_rel;
+    P.e_m = (float)(0.5 * (2.0 * s_rel + 12.0 * u) + 6.0 * u);
+    P.safety = 4.0f;
+    P.pz_tol = 2.5e-6f;
+    // stages: cuts whose outcome does not depend on the variation are decided per event
+    P.stage1 = 0;
+    P.stage2 = 0;
+    for (int c = 0; c < P.n_cuts; ++c) {
+        int k = P.kind[c];
+        bool s1 = k == CUT_NJETS_MIN || k == CUT_NBTAG_MIN || k == CUT_LEP_PT_MIN || k == CUT_LEP_OS ||
+                  k == CUT_W_NU_SOLVABLE || (k == CUT_MET_MIN && !P.smear_met);
+        if (s1) P.stage1 |= 1u << c;
+        else P.stage2 |= 1u << c;
+    }
+    P.n_exec2 = 0;
+    for (int c = 0; c < P.n_cuts; ++c)
+        if (P.stage2 >> c & 1u) P.exec2[P.n_exec2++] = c;
+    return HF_OK;
+}
+
+hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
+{
+    if (ctx->arena_bytes >= bytes) return HF_OK;
+    if (ctx->arena) {
+        HF_CUDA(cudaStreamSynchronize(ctx->s_comp));
+        if (ctx->arena_free) HF_CUDA(cudaEventSynchronize(ctx->arena_free));
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)64 << 20);
+    cudaError_t e = cudaMalloc((void**)&ctx->arena, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HF_ENOMEM, "scratch arena allocation failed");
+    }
+    ctx->arena_bytes = want;
+    return HF_OK;
+}
+
+// Enqueues one run on stream st with the device memory at `scratch`.
+hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint32_t V, const Out& Oin,
+                      char* scratch, const RunLayout& L, uint64_t seed, uint64_t first_id, bool plain,
+                      cudaStream_t st)
+{
+    Scratch S = make_scratch(scratch, L, A);
+    Out O = Oin;
+    if (!O.cutflow) O.cutflow = (unsigned long long*)(scratch + L.off_cutflow);
+    if (!O.hist) O.hist = (unsigned long long*)(scratch + L.off_hist);
+    if (!O.rc_total) O.rc_total = (unsigned long long*)(scratch + L.off_rctot);
+    HF_CUDA(cudaMemsetAsync(scratch + L.off_small, 0, 256, st));
+    HF_CUDA(cudaMemsetAsync(S.stats, 0, 8 * 3 * MAX_CUTS, st));
+    HF_CUDA(cudaMemsetAsync(O.cutflow, 0, 8 * (A.plan.n_cuts + 1), st));
+    HF_CUDA(cudaMemsetAsync(O.hist, 0, 8 * (A.plan.nbins + 2), st));
+    HF_CUDA(cudaMemsetAsync(O.rc_total, 0, 8, st));
+    if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per call");
+    if (N == 0) return HF_OK;
+    bool use_plain = plain || (ctx->flags & HF_FLAG_PLAIN);
+    if (use_plain) S.exec2 = nullptr;
+    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st));
+    if (!use_plain && A.sched) HF_CUDA(launch_sched_update(A.sched, S.stats, st));
+    if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
+    return HF_OK;
+}
+
+hf_status check_cols(const hf_columns* c, uint64_t N, int L)
+{
+    if (!c) return fail(HF_EINVAL, "columns are NULL");
+    if (N > 0 && (!c->jet_off || !c->btag || !c->lep || !c->lep_q || !c->met))
+        return fail(HF_EINVAL, "a column pointer is NULL");
+    if (N > 0 && c->n_jets_total > 0 && !c->jets) return fail(HF_EINVAL, "jets is NULL");
+    if (c->n_jets_total >= (1ull << 32)) return fail(HF_EINVAL, "at most 2^32 - 1 jets per chunk");
+    if (((uintptr_t)c->jets & 15) || ((uintptr_t)c->lep & 15) || ((uintptr_t)c->met & 7))
+        return fail(HF_EINVAL, "jets/lep must be 16-byte and met 8-byte aligned");
+    (void)L;
+    return HF_OK;
+}
+
+Analysis* get_analysis(hf_ctx* ctx, uint32_t id)
+{
+    if (id == 0 || id > ctx->analyses.size()) return nullptr;
+    return ctx->analyses[id - 1].get();
+}
+
+hf_status run_device_impl(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols, uint64_t N,
+                          uint64_t first_event_id, uint64_t seed, uint32_t V, const hf_results* dev_out,
+                          void* stream, bool plain)
+{
+    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    Analysis* A = get_analysis(ctx, analysis_id);
+    if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
+    if (V < 1 || V > 65535) return fail(HF_EINVAL, "n_variations must be 1..65535");
+    int L = A->plan.model == MODEL_DILEP ? 2 : 1;
+    if (hf_status s = check_cols(dev_cols, N, L)) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
+    RunLayout RL = layout_for(N, V);
+    if (hf_status s = ensure_arena(ctx, RL.scratch_bytes)) return s;
+    if (ctx->arena_free) HF_CUDA(cudaStreamWaitEvent(st, ctx->arena_free, 0));
+    Cols C;
+    C.jet_off = dev_cols->jet_off;
+    C.jets = (const float4*)dev_cols->jets;
+    C.btag = dev_cols->btag;
+    C.lep = (const float4*)dev_cols->lep;
+    C.lep_q = dev_cols->lep_q;
+    C.met = (const float2*)dev_cols->met;
+    C.n_jets_total = dev_cols->n_jets_total;
+    Out O;
+    memset(&O, 0, sizeof O);
+    if (dev_out) {
+        O.mask = dev_out->mask;
+        O.n_surv = dev_out->n_surv;
+        O.reco = (float4*)dev_out->reco;
+        O.cutflow = (unsigned long long*)dev_out->cutflow;
+        O.hist = (unsigned long long*)dev_out->hist;
+        O.rc_total = (unsigned long long*)dev_out->recheck_count;
+        if (dev_out->reco && ((uintptr_t)dev_out->reco & 15)) return fail(HF_EINVAL, "reco must be 16-byte aligned");
+    }
+    hf_status s = enqueue_run(ctx, *A, C, N, V, O, ctx->arena, RL, seed, first_event_id, plain, st);
+    if (s) return s;
+    if (!ctx->arena_free) HF_CUDA(cudaEventCreateWithFlags(&ctx->arena_free, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(ctx->arena_free, st));
+    return HF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hf_last_error(hf_ctx*) { return g_err.c_str(); }
+
+hf_status hf_open(const hf_config* cfg, hf_ctx** out)
+{
+    if (!out) return fail(HF_EINVAL, "out is NULL");
+    *out = nullptr;
+    hf_config def;
+    memset(&def, 0, sizeof def);
+    if (!cfg) cfg = &def;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(HF_EINVAL, "no such device");
+    std::unique_ptr<hf_ctx> ctx(new hf_ctx);
+    ctx->device = cfg->device;
+    ctx->flags = cfg->flags;
+    ctx->max_inflight = cfg->max_inflight ? cfg->max_inflight : 64;
+    HF_CUDA(cudaSetDevice(ctx->device));
+    HF_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking));
+    HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking));
+    HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking));
+    ctx->user_stream = (cudaStream_t)cfg->stream;
+    if (cfg->hbm_budget_bytes) {
+        ctx->budget = cfg->hbm_budget_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        HF_CUDA(cudaMemGetInfo(&fr, &tot));
+        ctx->budget = (uint64_t)(0.8 * (double)fr);
+    }
+    // keep freed stream-ordered memory cached in the pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+        uint64_t thr = ctx->budget;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = ctx.release();
+    return HF_OK;
+}
+
+hf_status hf_close(hf_ctx* ctx)
+{
+    if (!ctx) return HF_OK;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        // bounded wait for all streams
+        auto t0 = std::chrono::steady_clock::now();
+        cudaStream_t ss[3] = {ctx->s_h2d, ctx->s_comp, ctx->s_d2h};
+        for (cudaStream_t s : ss) {
+            while (cudaStreamQuery(s) == cudaErrorNotReady) {
+                if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+                    return fail(HF_ETIMEOUT, "in-flight work did not finish within 60 s");
+                std::this_thread::sleep_for(std::chrono::microseconds(200));
+            }
+        }
+        for (auto& kv : ctx->tickets) {
+            if (kv.second.dmem) cudaFree(kv.second.dmem);
+            if (kv.second.done) cudaEventDestroy(kv.second.done);
+        }
+        for (auto& a : ctx->analyses)
+            if (a->sched) cudaFree(a->sched);
+        if (ctx->arena) cudaFree(ctx->arena);
+        if (ctx->arena_free) cudaEventDestroy(ctx->arena_free);
+        cudaStreamDestroy(ctx->s_h2d);
+        cudaStreamDestroy(ctx->s_comp);
+        cudaStreamDestroy(ctx->s_d2h);
+    }
+    delete ctx;
+    return HF_OK;
+}
+
+hf_status hf_define_cuts(hf_ctx* ctx, const hf_analysis_desc* desc, uint32_t* analysis_id)
+{
+    if (!ctx || !analysis_id) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    std::unique_ptr<Analysis> A(new Analysis);
+    if (hf_status s = build_plan(desc, *A)) return s;
+    A->no_sched = (ctx->flags & HF_FLAG_NO_SCHED) != 0;
+    SchedDev sd;
+    memset(&sd, 0, sizeof sd);
+    const Plan& P = A->plan;
+    sd.n_exec2 = P.n_exec2;
+    sd.n_stage2 = P.n_exec2;
+    for (int i = 0; i < P.n_exec2; ++i) {
+        sd.exec2[i] = P.exec2[i];
+        sd.stage2_cuts[i] = P.exec2[i];
+    }
+    sd.stage2_mask = P.stage2;
+    for (int c = 0; c < P.n_cuts; ++c) {
+        sd.dep_mask[c] = desc->cuts[c].dep_mask;
+        sd.pinned[c] = desc->cuts[c].reorderable ? 0 : 1;
+    }
+    // implicit dependency: the Higgs window uses the two-neutrino pairing
+    for (int c = 0; c < P.n_cuts; ++c)
+        if (P.kind[c] == CUT_HIGGS_WINDOW)
+            for (int d = 0; d < P.n_cuts; ++d)
+                if (P.kind[d] == CUT_DILEP_SOLVABLE && d < c) sd.dep_mask[c] |= 1u << d;
+    sd.frozen = A->no_sched ? 1 : 0;
+    HF_CUDA(cudaMalloc((void**)&A->sched, sizeof(SchedDev)));
+    HF_CUDA(cudaMemcpy(A->sched, &sd, sizeof sd, cudaMemcpyHostToDevice));
+    ctx->analyses.push_back(std::move(A));
+    *analysis_id = (uint32_t)ctx->analyses.size();
+    return HF_OK;
+}
+
+hf_status hf_run_device(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols, uint64_t n_events,
+                        uint64_t first_event_id, uint64_t seed, uint32_t n_variations, const hf_results* dev_out,
+                        void* stream)
+{
+    return run_device_impl(ctx, analysis_id, dev_cols, n_events, first_event_id, seed, n_variations, dev_out,
+                           stream, false);
+}
+
+hf_status hf_run_device_plain(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols, uint64_t n_events,
+                              uint64_t first_event_id, uint64_t seed, uint32_t n_variations,
+                              const hf_results* dev_out, void* stream)
+{
+    return run_device_impl(ctx, analysis_id, dev_cols, n_events, first_event_id, seed, n_variations, dev_out,
+                           stream, true);
+}
+
+hf_status hf_device_error(hf_ctx* ctx, uint32_t* word)
+{
+    if (!ctx || !word) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    *word = 0;
+    if (!ctx->arena) return HF_OK;
+    if (ctx->arena_free) HF_CUDA(cudaEventSynchronize(ctx->arena_free));
+    HF_CUDA(cudaMemcpy(word, ctx->arena + SM_ERR, 4, cudaMemcpyDeviceToHost));
+    return HF_OK;
+}
+
+hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* hc, uint64_t N,
+                          uint64_t first_event_id, uint64_t seed, uint32_t V, uint64_t* ticket)
+{
+    if (!ctx || !ticket) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    Analysis* A = get_analysis(ctx, analysis_id);
+    if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
+    if (V < 1 || V > 65535) return fail(HF_EINVAL, "n_variations must be 1..65535");
+    const int L = A->plan.model == MODEL_DILEP ? 2 : 1;
+    if (hf_status s = check_cols(hc, N, L)) return s;
+    if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per chunk");
+    if (N > 0 && hc->jet_off[0] != 0) return fail(HF_EINVAL, "jet_off[0] must be 0");
+    if (N > 0 && hc->jet_off[N] != hc->n_jets_total) return fail(HF_EINVAL, "jet_off[N] != n_jets_total");
+    if (ctx->tickets.size() >= ctx->max_inflight) return fail(HF_EBUSY, "too many in-flight tickets");
+    const uint64_t J = hc->n_jets_total;
+    ColLayout CL = col_layout(N, J, L);
+    RunLayout RL = layout_for(N, V);
+    ResLayout RR = res_layout(N);
+    size_t bytes = CL.bytes + RL.scratch_bytes + RR.bytes;
+    if (ctx->inflight_bytes + bytes > ctx->budget) return fail(HF_EBUSY, "HBM budget exhausted; retry later");
+    Ticket T;
+    T.id = ctx->next_ticket++;
+    T.analysis = analysis_id;
+    T.N = N;
+    T.bytes = bytes;
+    T.L = RL;
+    T.R = RR;
+    cudaError_t e = cudaMallocAsync((void**)&T.dmem, bytes, ctx->s_h2d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HF_ENOMEM, "device allocation for the chunk failed");
+    }
+    char* dc = T.dmem;
+    char* dscr = T.dmem + CL.bytes;
+    char* dres = dscr + RL.scratch_bytes;
+    if (N > 0) {
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jets, hc->jets, 16 * J, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep, hc->lep, 16 * (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_met, hc->met, 8 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jet_off, hc->jet_off, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_btag, hc->btag, 2 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep_q, hc->lep_q, (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+    }
+    cudaEvent_t h2d;
+    HF_CUDA(cudaEventCreateWithFlags(&h2d, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(h2d, ctx->s_h2d));
+    HF_CUDA(cudaStreamWaitEvent(ctx->s_comp, h2d, 0));
+    cudaEventDestroy(h2d);
+    Cols C;
+    C.jet_off = (const uint32_t*)(dc + CL.off_jet_off);
+    C.jets = (const float4*)(dc + CL.off_jets);
+    C.btag = (const uint16_t*)(dc + CL.off_btag);
+    C.lep = (const float4*)(dc + CL.off_lep);
+    C.lep_q = (const int8_t*)(dc + CL.off_lep_q);
+    C.met = (const float2*)(dc + CL.off_met);
+    C.n_jets_total = J;
+    Out O;
+    memset(&O, 0, sizeof O);
+    O.mask = (uint8_t*)(dres + RR.off_mask);
+    O.n_surv = (uint16_t*)(dres + RR.off_nsurv);
+    O.reco = (float4*)(dres + RR.off_reco);
+    hf_status s = enqueue_run(ctx, *A, C, N, V, O, dscr, RL, seed, first_event_id, false, ctx->s_comp);
+    HF_CUDA(cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(T.done, ctx->s_comp));
+    if (s) T.failed_launch = true;
+    ctx->inflight_bytes += bytes;
+    *ticket = T.id;
+    ctx->tickets[T.id] = T;
+    return s;
+}
+
+hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state)
+{
+    if (!ctx || !state) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(HF_ENOTFOUND, "unknown ticket");
+    if (it->second.failed_launch) {
+        *state = HF_STATE_FAILED;
+        return HF_OK;
+    }
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaEventQuery(it->second.done);
+    if (e == cudaSuccess) *state = HF_STATE_DONE;
+    else if (e == cudaErrorNotReady) *state = HF_STATE_RUNNING;
+    else {
+        *state = HF_STATE_FAILED;
+        return cuda_fail(e, "cudaEventQuery");
+    }
+    return HF_OK;
+}
+
+hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32_t timeout_ms)
+{
+    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    cudaEvent_t done;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->tickets.find(ticket);
+        if (it == ctx->tickets.end()) return fail(HF_ENOTFOUND, "unknown ticket");
+        done = it->second.done;
+    }
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaEventQuery(done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the chunk");
+        if (std::chrono::steady_clock::now() - t0 >= std::chrono::milliseconds(timeout_ms))
+            return fail(HF_ETIMEOUT, "chunk not finished within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(HF_ENOTFOUND, "unknown ticket");
+    Ticket T = it->second;
+    ctx->tickets.erase(it);
+    ctx->inflight_bytes -= T.bytes;
+    Analysis* A = get_analysis(ctx, T.analysis);
+    const int L = A->plan.model == MODEL_DILEP ? 2 : 1;
+    (void)L;
+    char* dscr = T.dmem + (T.bytes - T.L.scratch_bytes - T.R.bytes);
+    char* dres = dscr + T.L.scratch_bytes;
+    hf_status st = HF_OK;
+    unsigned err = 0;
+    cudaError_t e = cudaMemcpy(&err, dscr + T.L.off_small + SM_ERR, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = cuda_fail(e, "reading the error word");
+    if (!st && T.failed_launch) st = fail(HF_ECUDA, "the chunk's launch failed");
+    if (!st && (err & ERR_COLUMNS)) st = fail(HF_EINVAL, "malformed columns (offsets or n_jets > 12)");
+    if (!st && out) {
+        const uint64_t N = T.N;
+        const int nc = A->plan.n_cuts, nb = A->plan.nbins;
+        cudaStream_t s = ctx->s_d2h;
+        if (out->mask && N) e = cudaMemcpyAsync(out->mask, dres + T.R.off_mask, N, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->n_surv && N)
+            e = cudaMemcpyAsync(out->n_surv, dres + T.R.off_nsurv, 2 * N, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->reco && N)
+            e = cudaMemcpyAsync(out->reco, dres + T.R.off_reco, 16 * N, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->cutflow)
+            e = cudaMemcpyAsync(out->cutflow, dscr + T.L.off_cutflow, 8 * (nc + 1), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->hist)
+            e = cudaMemcpyAsync(out->hist, dscr + T.L.off_hist, 8 * (nb + 2), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->recheck_count)
+            e = cudaMemcpyAsync(out->recheck_count, dscr + T.L.off_rctot, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copying results");
+    }
+    cudaFreeAsync(T.dmem, ctx->s_d2h);
+    cudaEventDestroy(T.done);
+    return st;
+}
+
+hf_status hf_sched_state(hf_ctx* ctx, uint32_t analysis_id, int32_t* exec_order, uint64_t* evaluated,
+                         uint64_t* passed, uint64_t* cost)
+{
+    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    Analysis* A = get_analysis(ctx, analysis_id);
+    if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
+    HF_CUDA(cudaStreamSynchronize(ctx->s_comp));
+    if (ctx->arena_free) HF_CUDA(cudaEventSynchronize(ctx->arena_free));
+    SchedDev sd;
+    HF_CUDA(cudaMemcpy(&sd, A->sched, sizeof sd, cudaMemcpyDeviceToHost));
+    const Plan& P = A->plan;
+    if (exec_order) {
+        // full execution order: stage-1 cuts (evaluated together per event) in user
+        // order, then the stage-2 cuts in their current execution order
+        int k = 0;
+        for (int c = 0; c < P.n_cuts; ++c)
+            if (P.stage1 >> c & 1u) exec_order[k++] = c;
+        for (int i = 0; i < sd.n_exec2; ++i) exec_order[k++] = sd.exec2[i];
+    }
+    for (int c = 0; c < P.n_cuts; ++c) {
+        if (evaluated) evaluated[c] = sd.tot_eval[c];
+        if (passed) passed[c] = sd.tot_pass[c];
+        if (cost) cost[c] = sd.tot_cost[c];
+    }
+    return HF_OK;
+}
+
+hf_status hf_set_exec_order(hf_ctx* ctx, uint32_t analysis_id, const int32_t* order)
+{
+    if (!ctx || !order) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    Analysis* A = get_analysis(ctx, analysis_id);
+    if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
+    const Plan& P = A->plan;
+    unsigned seen = 0;
+    for (int x = 0; x < P.n_cuts; ++x) {
+        int c = order[x];
+        if (c < 0 || c >= P.n_cuts || (seen >> c & 1u)) return fail(HF_EINVAL, "not a permutation of the cuts");
+        unsigned deps = A->cuts[c].dep_mask;
+        if ((deps & ~seen) != 0u) return fail(HF_EINVAL, "order violates a dependency");
+        seen |= 1u << c;
+    }
+    SchedDev sd;
+    HF_CUDA(cudaStreamSynchronize(ctx->s_comp));
+    if (ctx->arena_free) HF_CUDA(cudaEventSynchronize(ctx->arena_free));
+    HF_CUDA(cudaMemcpy(&sd, A->sched, sizeof sd, cudaMemcpyDeviceToHost));
+    int k = 0;
+    for (int x = 0; x < P.n_cuts; ++x)
+        if (P.stage2 >> order[x] & 1u) sd.exec2[k++] = order[x];
+    sd.n_exec2 = k;
+    sd.frozen = 1;
+    HF_CUDA(cudaMemcpy(A->sched, &sd, sizeof sd, cudaMemcpyHostToDevice));
+    return HF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// hf_fp64.cuh -- FP64 evaluation of one unit on the GPU (the recheck path).
+//
+// Units whose FP32 evaluation lands within an error band of a decision are
+// evaluated again here, in double precision, with the definition's
+// formulation and operation order (compiled with -fmad=false: every + - * /
+// is one IEEE rounding in the order written; division and sqrt are
+// correctly rounded).  The results therefore coincide with any FP64
+// implementation of the same formulation, apart from the transcendental
+// functions of the Box-Muller transform (log, sin, cos), whose CUDA and host
+// implementations may differ in the last bit.
+//
+// Definitions (HEP-Frame, arXiv:2211.14346): W-mass neutrino p_z with MET as
+// the neutrino pT (Sect. 6.2); hadronic-top chi-square, Eq. 1 (Sect. 6.2);
+// two-neutrino solution from the W- and top-mass constraints and the Higgs
+// b-jet pair (Sect. 4); smearing pseudo-experiments (Sect. 4).
+#pragma once
+#include "hf_dev.cuh"
+#include <math_constants.h>
+
+namespace hf {
+
+struct EvD {
+    int n;
+    double jet[MAX_JETS][4];  // smeared jets (px, py, pz, E)
+    unsigned btag;
+    double lep[2][4];
+    int q[2];
+    double metx, mety;        // smeared MET
+};
+
+__device__ __forceinline__ void v4_add_d(const double* a, const double* b, double* o)
+{
+    o[0] = a[0] + b[0];
+    o[1] = a[1] + b[1];
+    o[2] = a[2] + b[2];
+    o[3] = a[3] + b[3];
+}
+__device__ __forceinline__ double m2_d(const double* a)
+{
+    return a[3] * a[3] - (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+}
+__device__ __forceinline__ double mass_d(const double* a)
+{
+    double m2 = m2_d(a);
+    return m2 >= 0.0 ? sqrt(m2) : -sqrt(-m2);
+}
+
+// Smearing normals of one unit in FP64: Philox words (b, v, e_lo, e_hi),
+// Box-Muller pairs z[2k] = r cos(2 pi u1), z[2k+1] = r sin(2 pi u1).
+__device__ inline void unit_normals_d(uint64_t seed, uint64_t event, uint32_t v, double z[16])
+{
+    const double two_pi = 2.0 * 3.141592653589793;
+    uint2 key = key_of(seed);
+    for (uint32_t b = 0; b < 4; ++b) {
+        uint4 w = philox4x32_10(ctr_of(b, v, event), key);
+        uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+        for (int k = 0; k < 2; ++k) {
+            double u0 = u01d(ww[2 * k]);
+            double u1 = u01d(ww[2 * k + 1]);
+            double r = sqrt(-2.0 * log(u0));
+            double th = two_pi * u1;
+            z[4 * b + 2 * k] = r * cos(th);
+            z[4 * b + 2 * k + 1] = r * sin(th);
+        }
+    }
+}
+
+// Loads event e and applies the smearing of variation v.
+__device__ inline void load_event_d(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id,
+                                    uint64_t seed, uint32_t v, EvD& ev)
+{
+    uint32_t j0 = C.jet_off[e];
+    ev.n = (int)(C.jet_off[e + 1] - j0);
+    ev.btag = C.btag[e];
+    int L = P.model == MODEL_DILEP ? 2 : 1;
+    for (int l = 0; l < L; ++l) {
+        float4 lf = C.lep[(uint64_t)e * L + l];
+        ev.lep[l][0] = lf.x;
+        ev.lep[l][1] = lf.y;
+        ev.lep[l][2] = lf.z;
+        ev.lep[l][3] = lf.w;
+        ev.q[l] = C.lep_q[(uint64_t)e * L + l];
+    }
+    float2 mf = C.met[e];
+    double z[16];
+    bool smear = P.dsigma_jet != 0.0 || P.dsigma_met != 0.0;
+    if (smear) unit_normals_d(seed, event_id, v, z);
+    for (int i = 0; i < ev.n; ++i) {
+        float4 jf = C.jets[j0 + i];
+        double s = smear ? 1.0 + P.dsigma_jet * z[i] : 1.0;
+        double js[4] = {jf.x, jf.y, jf.z, jf.w};
+        for (int c = 0; c < 4; ++c) ev.jet[i][c] = smear ? s * js[c] : js[c];
+    }
+    ev.metx = smear ? (double)mf.x + P.dsigma_met * z[12] : (double)mf.x;
+    ev.mety = smear ? (double)mf.y + P.dsigma_met * z[13] : (double)mf.y;
+}
+
+// W-mass neutrino p_z (massless lepton and neutrino):
+//   mu = mW^2/2 + pT(l).pT(nu), a = E_l^2 - pz_l^2, D = mu^2 - a pT(nu)^2;
+// smaller-|p_z| root without cancellation, or the real part mu pz_l / a when
+// D < 0; solvable iff a > 0 and the result is finite.
+__device__ inline int w_pz_d(const double* lep, double metx, double mety, double mW, double* pz_out)
+{
+    double lx = lep[0], ly = lep[1], lz = lep[2], lE = lep[3];
+    double mu = mW * mW / 2.0 + (lx * metx + ly * mety);
+    double a = lE * lE - lz * lz;
+    double pt2 = metx * metx + mety * mety;
+    double D = mu * mu - a * pt2;
+    double pz;
+    if (!(a > 0.0)) {
+        *pz_out = 0.0;
+        return 0;
+    }
+    if (D < 0.0) {
+        pz = mu * lz / a;
+    } else {
+        double t = mu * lz;
+        double sq = lE * sqrt(D);
+        double q = t >= 0.0 ? t + sq : t - sq;
+        pz = q == 0.0 ? 0.0 : (lE * lE * pt2 - mu * mu) / q;
+    }
+    *pz_out = pz;
+    return isfinite(pz) ? 1 : 0;
+}
+
+// Hadronic-top triplet chi-square, Eq. 1: enumeration k, then i < j, k not in
+// {i, j}; strict minimum, ties to the first; n < 3 -> +inf.
+__device__ inline double hadtop_d(const EvD& ev, const Plan& P, double* mtop, double* mw)
+{
+    double best = CUDART_INF;
+    *mtop = 0.0;
+    *mw = 0.0;
+    for (int k = 0; k < ev.n; ++k)
+        for (int i = 0; i < ev.n; ++i) {
+            if (i == k) continue;
+            for (int j = i + 1; j < ev.n; ++j) {
+                if (j == k) continue;
+                double W[4], T[4];
+                v4_add_d(ev.jet[i], ev.jet[j], W);
+                v4_add_d(W, ev.jet[k], T);
+                double m_w = mass_d(W);
+                double m_t = mass_d(T);
+                double dt = (m_t - P.dmt) / P.dsigma_t;
+                double dw = (m_w - P.dmW) / P.dsigma_W;
+                double chi2 = dt * dt + dw * dw;
+                if (chi2 < best) {
+                    best = chi2;
+                    *mtop = m_t;
+                    *mw = m_w;
+                }
+            }
+        }
+    return best;
+}
+
+}  // namespace hf

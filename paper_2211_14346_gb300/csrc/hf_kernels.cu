@@ -1,0 +1,167 @@
+// hf_kernels.cu -- scan, compaction and FP64 recheck of the cut chain, and
+// the launch sequence of one run.
+//
+// Pipeline of one run (all on one stream, no host synchronisation):
+//   k_count      jet-multiplicity histogram of the chunk (bucket capacities)
+//   k_stage1     per event: validation, the cuts that do not depend on the
+//                smearing variation (exact: FP32 with an FP64 fallback inside
+//                the rounding band), cut flow of the events decided here, and
+//                compaction of the rest into per-multiplicity buckets
+//                (shared-memory counters, one global atomic per bucket per block)
+//   k_stage2_*<N> one persistent grid per jet multiplicity N, largest first
+//                (hf_stage2_semi.cuh)
+//   k_recheck    FP64 re-evaluation of the listed units, then completion of
+//                their events
+// Cut flow and histogram are integer counts reduced in shared memory and
+// added to global u64 counters once per block.
+#include "hf_common.cuh"
+#include "hf_kernels.h"
+
+namespace hf {
+
+// ------------------------------------------------------------------ k_count
+__global__ void k_count(const Cols C, uint32_t N, Scratch S)
+{
+    __shared__ unsigned h[16];
+    if (threadIdx.x < 16) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+        uint32_t a = C.jet_off[e], b = C.jet_off[e + 1];
+        uint32_t n = b - a;
+        if (b >= a && n <= MAX_JETS) atomicAdd(&h[n], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NBUCKET && h[threadIdx.x]) atomicAdd(&S.nhist[threadIdx.x], h[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------ k_stage1
+__global__ void __launch_bounds__(256) k_stage1(const Plan P, const Cols C, uint32_t N, uint32_t V,
+                                                const Out O, Scratch S)
+{
+    __shared__ unsigned s_base[16], s_cnt[16], s_off[16];
+    __shared__ unsigned long long s_fc[MAX_CUTS + 1];
+    if (threadIdx.x < 16) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x <= MAX_CUTS) s_fc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int b = 0; b < NBUCKET; ++b) {
+            s_base[b] = acc;
+            acc += S.nhist[b];
+        }
+    }
+    __syncthreads();
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    int bucket = -1;
+    unsigned loc = 0, bits = 0;
+    if (e < N) {
+        uint32_t a = C.jet_off[e], b = C.jet_off[e + 1];
+        uint32_t n = b - a;
+        if (b < a || n > MAX_JETS || (uint64_t)b > C.n_jets_total) {
+            atomicOr(S.err, ERR_COLUMNS);
+            write_zero_event(O, e);
+        } else {
+            bits = stage1_bits(P, C, e, (int)n);
+            int f1 = first_fail_stage1(P, bits);
+            if (needs_stage2(P, f1)) {
+                bucket = (int)n;
+                loc = atomicAdd(&s_cnt[n], 1u);
+            } else {
+                atomicAdd(&s_fc[f1], (unsigned long long)V);
+                write_zero_event(O, e);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NBUCKET && s_cnt[threadIdx.x])
+        s_off[threadIdx.x] = atomicAdd(&S.cursor[threadIdx.x], s_cnt[threadIdx.x]);
+    __syncthreads();
+    if (bucket >= 0) S.bucket[s_base[bucket] + s_off[bucket] + loc] = make_uint2(e, bits);
+    flush_cutflow(P, O, s_fc);
+}
+
+// ------------------------------------------------------------------ recheck
+__global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, const Out O, Scratch S,
+                                                   uint64_t seed, uint64_t first_id)
+{
+    __shared__ unsigned long long s_fc[MAX_CUTS + 1];
+    __shared__ unsigned s_hist[MAX_BINS + 2];
+    __shared__ unsigned s_n;
+    if (threadIdx.x <= MAX_CUTS) s_fc[threadIdx.x] = 0;
+    for (int b = threadIdx.x; b < P.nbins + 2; b += blockDim.x) s_hist[b] = 0;
+    if (threadIdx.x == 0) s_n = *S.rc_valid;
+    __syncthreads();
+    const unsigned n = s_n;
+    unsigned long long mine = 0;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        RcEntry r = S.rc[i];
+        float4 reco;
+        int bin = 0;
+        int f = unit_fp64(P, C, r.event, first_id + r.event, seed, r.v, r.s1bits, &reco, &bin);
+        ++mine;
+        atomicAdd(&s_fc[f], 1ull);
+        if (f == P.n_cuts) {
+            atomicAdd(&s_hist[bin], 1u);
+            atomicAdd(&S.pend_cnt[r.slot], 1u);
+            atomicAdd(&S.pend_sum[r.slot].x, reco.x);
+            atomicAdd(&S.pend_sum[r.slot].y, reco.y);
+            atomicAdd(&S.pend_sum[r.slot].z, reco.z);
+            atomicAdd(&S.pend_sum[r.slot].w, reco.w);
+        }
+        __threadfence();
+        unsigned left = atomicSub(&S.pend_left[r.slot], 1u);
+        if (left == 1u) {
+            __threadfence();
+            unsigned cnt = atomicAdd(&S.pend_cnt[r.slot], 0u);
+            float4 sum, comp = S.pend_comp[r.slot];
+            sum.x = atomicAdd(&S.pend_sum[r.slot].x, 0.f);
+            sum.y = atomicAdd(&S.pend_sum[r.slot].y, 0.f);
+            sum.z = atomicAdd(&S.pend_sum[r.slot].z, 0.f);
+            sum.w = atomicAdd(&S.pend_sum[r.slot].w, 0.f);
+            write_event(O, r.event, cnt, sum, comp);
+        }
+    }
+    if (mine) atomicAdd(O.rc_total, mine);
+    __syncthreads();
+    flush_cutflow(P, O, s_fc);
+    flush_hist(P, O, s_hist);
+}
+
+// ------------------------------------------------------------------ host launchers
+int ev_per_tile_for(uint32_t V)
+{
+    int e = UNITS_PER_TILE / (int)V;
+    if (e < 1) e = 1;
+    if (e > MAX_EV_PER_TILE) e = MAX_EV_PER_TILE;
+    return e;
+}
+
+typedef cudaError_t (*S2Launcher)(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t, uint64_t,
+                                  uint64_t, int, int, cudaStream_t);
+
+cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
+                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st)
+{
+    if (N == 0) return cudaSuccess;
+    const unsigned nb = (N + 255) / 256;
+    cudaError_t e;
+    if (plain) {
+        e = launch_plain(P, C, N, V, O, S, seed, first_id, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_count<<<min(nb, 4096u), 256, 0, st>>>(C, N, S);
+        k_stage1<<<nb, 256, 0, st>>>(P, C, N, V, O, S);
+        const int ept = ev_per_tile_for(V);
+        static const S2Launcher semi[NBUCKET] = {
+            launch_s2_semi<0>, launch_s2_semi<1>, launch_s2_semi<2>,  launch_s2_semi<3>, launch_s2_semi<4>,
+            launch_s2_semi<5>, launch_s2_semi<6>, launch_s2_semi<7>,  launch_s2_semi<8>, launch_s2_semi<9>,
+            launch_s2_semi<10>, launch_s2_semi<11>, launch_s2_semi<12>};
+        for (int n = NBUCKET - 1; n >= 0; --n) {
+            e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    k_recheck<<<sms * 4, BLOCK, 0, st>>>(P, C, O, S, seed, first_id);
+    return cudaGetLastError();
+}
+
+}  // namespace hf

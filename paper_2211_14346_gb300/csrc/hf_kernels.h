@@ -1,0 +1,24 @@
+// hf_kernels.h -- host-side entry points of the device code (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hf_dev.cuh"
+
+namespace hf {
+
+// Events per tile of the stage-2 kernels for V variations per event.
+int ev_per_tile_for(uint32_t V);
+
+// Enqueues one whole run of the path on stream st.  Scratch counters and the
+// output accumulators must be zeroed by the caller beforehand.
+template <int N>
+cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+                           uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st);
+
+cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
+                         uint64_t seed, uint64_t first_id, cudaStream_t st);
+
+cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
+                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st);
+
+}  // namespace hf

@@ -1,0 +1,320 @@
+// hf_semilep.cuh -- FP32 evaluation of one semileptonic unit with error
+// bands (device code, templated on the jet multiplicity N so that the
+// per-event Gram matrix, the jet scales and the triplet loop live in
+// registers).
+//
+// Definitions (HEP-Frame, arXiv:2211.14346, Sect. 6.2): neutrino p_z from the
+// W-mass constraint with MET as the neutrino pT; hadronic-top chi-square of
+// Eq. 1: chi2 = ((m_jjj - m_t)/sigma_t)^2 + ((m_jj - m_W)/sigma_W)^2,
+// minimised over jet triplets (k the b, {i < j} the W).
+//
+// GPU formulation: with the Minkowski Gram matrix G_ab = p_a . p_b of the
+// event's jets (computed once per event, compensated), a smeared triplet has
+//   m^2_ijk = sum_a s_a^2 G_aa + 2 sum_{a<b} s_a s_b G_ab  (a, b in {i, j, k}),
+// a sum of non-negative terms for physical jets, so its FP32 relative error
+// is a few ulp plus twice the error of the jet scales s; the bands below
+// bound |q32 - q64| for every quantity that decides a cut, an argmin, or a
+// histogram bin, and a unit inside any band is re-evaluated in FP64.
+#pragma once
+#include "hf_dev.cuh"
+#include "hf_fp64.cuh"
+#include <math_constants.h>
+
+namespace hf {
+
+struct UnitOut {
+    int f;        // cuts passed in user order (n_cuts = survives); -1 = recheck
+    float4 reco;  // (m_top, m_W, pz_nu, |MET|) when f == n_cuts
+    int bin;      // histogram bin when f == n_cuts
+};
+
+// Band of an FP32 chi2 value: |chi2_32 - chi2_64| bound using only the value
+// (|dt|, |dw| <= sqrt(chi2); masses <= centre + width sqrt(chi2)).
+__device__ __forceinline__ float chi2_band(const Plan& P, float c)
+{
+    if (!(c < 3.0e38f)) return 0.0f;
+    const float u = 5.9604645e-8f;  // 2^-24
+    float r = sqrtf(c);
+    float ddt = (P.e_m * (P.mt + P.sigma_t * r) + u * P.mt) * P.inv_sigma_t + 2.0f * u * r;
+    float ddw = (P.e_m * (P.mW + P.sigma_W * r) + u * P.mW) * P.inv_sigma_W + 2.0f * u * r;
+    float d = ddt + ddw;
+    return P.safety * (2.0f * r * d + d * d + 3.0f * u * c);
+}
+
+// Minimum and second minimum of the triplet chi2, with the masses of the
+// minimising candidate.  g: packed Gram matrix, s: jet scales.
+template <int N>
+__device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict__ g,
+                                         const float (&s)[N > 0 ? N : 1], float& b1, float& b2,
+                                         float& mt_b, float& mw_b)
+{
+    b1 = CUDART_INF_F;
+    b2 = CUDART_INF_F;
+    mt_b = 0.0f;
+    mw_b = 0.0f;
+    if constexpr (N >= 3) {
+        float a[N];
+        float q2[ntri(N)];
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), g[tri(i, i)]);
+#pragma unroll
+        for (int j = 1; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < j; ++i)
+                q2[tri(i, j)] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), g[tri(i, j)]);
+        const float c_t = -P.mt * P.inv_sigma_t;
+        const float c_w = -P.mW * P.inv_sigma_W;
+#pragma unroll
+        for (int j = 1; j < N; ++j) {
+#pragma unroll
+            for (int i = 0; i < j; ++i) {
+                float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2[tri(i, j)]);
+                float mw = __fmul_rn(pw, rsqrtf(pw));
+                float dw = fmaf(mw, P.inv_sigma_W, c_w);
+                float cw = __fmul_rn(dw, dw);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    if (k == i || k == j) continue;
+                    const int ik = k < i ? tri(k, i) : tri(i, k);
+                    const int jk = k < j ? tri(k, j) : tri(j, k);
+                    float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2[ik]), q2[jk]);
+                    float mt = __fmul_rn(m2, rsqrtf(m2));
+                    float dt = fmaf(mt, P.inv_sigma_t, c_t);
+                    float c = fmaf(dt, dt, cw);
+                    bool better = c < b1;
+                    b2 = fminf(b2, fmaxf(b1, c));
+                    mt_b = better ? mt : mt_b;
+                    mw_b = better ? mw : mw_b;
+                    b1 = fminf(b1, c);
+                }
+            }
+        }
+    }
+}
+
+// Float-float (unevaluated sum hi + lo) arithmetic, relative accuracy about
+// 2^-44 per operation (Dekker 1971; TwoProduct with fmaf).
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ ff ff_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    return ff{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_norm(float s, float e)
+{
+    float h = __fadd_rn(s, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return ff_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    ff p = ff_prod(a.h, b.h);
+    return ff_norm(p.h, __fadd_rn(p.l, fmaf(a.h, b.l, __fmul_rn(a.l, b.h))));
+}
+
+// W-mass neutrino p_z with mu, D and the numerator in float-float and a
+// running error bound that includes the error of the FP32-smeared MET
+// (dmx, dmy).  Returns false when the discriminant's sign is uncertain or the
+// bound exceeds pz_tol |p(nu)| (|p_z| + pT bounds the neutrino momentum);
+// the caller then takes the FP64 value.
+__device__ __forceinline__ bool w_pz_f(const Plan& P, float4 l, float mx, float my, float dmx, float dmy,
+                                       float& pz)
+{
+    const float u = 5.9604645e-8f;   // 2^-24
+    const float u2 = 9.094947e-13f;  // 2^-40: a few float-float operations
+    ff mu = ff_add(ff_add(ff{P.mW2half, P.mW2half_lo}, ff_prod(l.x, mx)), ff_prod(l.y, my));
+    ff el2 = ff_prod(l.w, l.w);
+    ff a = ff_sub(el2, ff_prod(l.z, l.z));
+    ff pt2 = ff_add(ff_prod(mx, mx), ff_prod(my, my));
+    ff mu2 = ff_mul(mu, mu);
+    ff D = ff_sub(mu2, ff_mul(a, pt2));
+    ff num = ff_sub(ff_mul(el2, pt2), mu2);
+    const float amu = fabsf(mu.h), af = a.h, apt2 = pt2.h;
+    float e_mu = fabsf(l.x) * dmx + fabsf(l.y) * dmy + u2 * (P.mW2half + fabsf(l.x * mx) + fabsf(l.y * my));
+    float e_pt2 = 2.0f * (fabsf(mx) * dmx + fabsf(my) * dmy) + dmx * dmx + dmy * dmy + u2 * apt2;
+    float e_a = u2 * (el2.h + l.z * l.z);
+    float e_D = 2.0f * amu * e_mu + e_mu * e_mu + af * e_pt2 + apt2 * e_a + u2 * (amu * amu + af * apt2);
+    float e_num = el2.h * e_pt2 + 2.0f * amu * e_mu + e_mu * e_mu + u2 * (el2.h * apt2 + amu * amu);
+    if (!(af > 0.0f)) { pz = 0.0f; return false; }
+    const float Df = __fadd_rn(D.h, D.l);
+    if (fabsf(Df) <= P.safety * e_D) return false;
+    float e_pz;
+    if (Df < 0.0f) {
+        pz = __fdiv_rn(__fmul_rn(mu.h, l.z), af);
+        e_pz = (fabsf(l.z) * e_mu + fabsf(pz) * e_a) / af + 4.0f * u * fabsf(pz);
+    } else {
+        float sD = sqrtf(Df);
+        float e_sD = e_D / (2.0f * sD) + u * sD;
+        float t = __fmul_rn(mu.h, l.z);
+        float sq = __fmul_rn(l.w, sD);
+        float q = t >= 0.0f ? __fadd_rn(t, sq) : __fsub_rn(t, sq);
+        if (q == 0.0f) return false;
+        float e_q = fabsf(l.z) * e_mu + l.w * e_sD + 3.0f * u * fabsf(q);
+        float nf = __fadd_rn(num.h, num.l);
+        pz = __fdiv_rn(nf, q);
+        e_pz = (e_num + u * fabsf(nf) + fabsf(pz) * e_q) / fabsf(q) + u * fabsf(pz);
+    }
+    return e_pz <= P.pz_tol * (fabsf(pz) + sqrtf(apt2));
+}
+
+// p_z in FP64 with the MET smeared in FP64 (the definition's arithmetic):
+// used when the FP32 bound is too wide, typically near D = 0 where p_z is
+// ill-conditioned in MET.  Does not affect any cut decision.
+static __device__ __noinline__ float w_pz_fp64(const Plan& P, float4 l, float2 met, uint64_t seed, uint64_t event_id,
+                                        uint32_t v)
+{
+    double mx = met.x, my = met.y;
+    if (P.smear_met || P.smear_jets) {
+        uint4 w = philox4x32_10(ctr_of(3, v, event_id), key_of(seed));
+        double u0 = u01d(w.x), u1 = u01d(w.y);
+        double r = sqrt(-2.0 * log(u0));
+        double th = (2.0 * 3.141592653589793) * u1;
+        mx = (double)met.x + P.dsigma_met * (r * cos(th));
+        my = (double)met.y + P.dsigma_met * (r * sin(th));
+    }
+    double lep[4] = {l.x, l.y, l.z, l.w};
+    double pz;
+    w_pz_d(lep, mx, my, P.dmW, &pz);
+    return (float)pz;
+}
+
+// Per-event inputs of a semileptonic unit.
+template <int N>
+struct SemiEvent {
+    const float* g;  // packed Gram matrix (shared memory, or local memory in the plain form)
+    float4 lep;
+    float2 met;
+    unsigned s1bits;
+    uint64_t event_id;
+};
+
+// Scheduler statistics of one block (shared memory).
+struct CutStats {
+    unsigned evaluated[MAX_CUTS];
+    unsigned passed[MAX_CUTS];
+    unsigned long long cost[MAX_CUTS];
+};
+
+// FP32 evaluation of one semileptonic unit.  exec: stage-2 cuts in execution
+// order.  After the first failure in execution order, the stage-2 cuts that
+// precede the earliest known failure in USER order and were not evaluated are
+// evaluated in user order, so that the reported number of leading cuts passed
+// is the user-order one whatever the execution order.
+template <int N>
+__device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const SemiEvent<N>& ev,
+                               uint32_t v, uint64_t seed, CutStats* st)
+{
+    UnitOut out;
+    out.f = -1;
+    out.reco = make_float4(0.f, 0.f, 0.f, 0.f);
+    out.bin = 0;
+    float s[N > 0 ? N : 1];
+#pragma unroll
+    for (int i = 0; i < (N > 0 ? N : 1); ++i) s[i] = 1.0f;
+    float mx = ev.met.x, my = ev.met.y, dmx = 0.0f, dmy = 0.0f;
+    const uint2 key = key_of(seed);
+    if (P.smear_jets) {
+#pragma unroll
+        for (int b = 0; b < (N + 3) / 4; ++b) {
+            uint4 w = philox4x32_10(ctr_of(b, v, ev.event_id), key);
+            float z0, z1, z2, z3;
+            box_muller_f(w.x, w.y, z0, z1);
+            if (4 * b + 0 < N) s[4 * b + 0] = fmaf(P.sigma_jet, z0, 1.0f);
+            if (4 * b + 1 < N) s[4 * b + 1] = fmaf(P.sigma_jet, z1, 1.0f);
+            if (4 * b + 2 < N) {
+                box_muller_f(w.z, w.w, z2, z3);
+                s[4 * b + 2] = fmaf(P.sigma_jet, z2, 1.0f);
+                if (4 * b + 3 < N) s[4 * b + 3] = fmaf(P.sigma_jet, z3, 1.0f);
+            }
+        }
+    }
+    if (P.smear_met) {
+        uint4 w = philox4x32_10(ctr_of(3, v, ev.event_id), key);
+        float z12, z13;
+        box_muller_f(w.x, w.y, z12, z13);
+        mx = fmaf(P.sigma_met, z12, ev.met.x);
+        my = fmaf(P.sigma_met, z13, ev.met.y);
+        const float u = 5.9604645e-8f;
+        dmx = P.sigma_met * P.z_rel * fabsf(z12) + u * fabsf(mx);
+        dmy = P.sigma_met * P.z_rel * fabsf(z13) + u * fabsf(my);
+    }
+    float b1 = CUDART_INF_F, b2 = CUDART_INF_F, mt_b = 0.f, mw_b = 0.f;
+    bool top_done = false;
+    float met = 0.f, met_err = 0.f;
+    bool met_done = false;
+    unsigned evald = 0, passd = 0;
+    // first stage-1 failure (user order) bounds the cuts that matter
+    const unsigned s1fail = P.stage1 & ~ev.s1bits;
+    bool phase1 = true;
+    int x = 0;
+    int f = P.n_cuts;
+    while (true) {
+        int c;
+        unsigned fails = s1fail | (evald & ~passd);
+        int kf = fails ? __ffs(fails) - 1 : P.n_cuts;
+        if (phase1) {
+            if (x >= nexec) { phase1 = false; continue; }
+            c = exec[x++];
+            if (c > kf) continue;
+        } else {
+            unsigned below = kf >= 32 ? 0xffffffffu : ((1u << kf) - 1u);
+            unsigned todo = P.stage2 & ~evald & below;
+            if (!todo) { f = kf; break; }
+            c = __ffs(todo) - 1;
+        }
+        long long t0 = clock64();
+        bool pass = false, unsure = false;
+        const int kind = P.kind[c];
+        if (kind == CUT_MET_MIN) {
+            if (!met_done) {
+                met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
+                met_err = P.safety * (dmx + dmy + 3.6e-7f * met);
+                met_done = true;
+            }
+            pass = met > P.p0[c];
+            unsure = fabsf(met - P.p0[c]) <= met_err;
+        } else if (kind == CUT_HADTOP_CHI2_MAX) {
+            if (!top_done) {
+                hadtop_f<N>(P, ev.g, s, b1, b2, mt_b, mw_b);
+                top_done = true;
+            }
+            pass = b1 < P.p0[c];
+            unsure = fabsf(b1 - P.p0[c]) <= chi2_band(P, b1);
+        }
+        if (st) {
+            long long dt = clock64() - t0;
+            atomicAdd(&st->evaluated[c], 1u);
+            if (pass) atomicAdd(&st->passed[c], 1u);
+            atomicAdd(&st->cost[c], (unsigned long long)(dt > 0 ? dt : 0));
+        }
+        if (unsure) return out;  // f = -1: FP64 recheck
+        evald |= 1u << c;
+        if (pass) passd |= 1u << c;
+        else phase1 = false;
+    }
+    if (f == P.n_cuts) {
+        // survivor: reconstructed quantities must be certain as well
+        if (!top_done) return out;  // (the model always has the chi2 cut)
+        if (b2 - b1 <= chi2_band(P, b1) + chi2_band(P, b2)) return out;  // argmin near-tie
+        float pz;
+        if (!w_pz_f(P, ev.lep, mx, my, dmx, dmy, pz)) pz = w_pz_fp64(P, ev.lep, ev.met, seed, ev.event_id, v);
+        if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
+        bool hu = false;
+        int bin = hist_bin_f(P, mt_b, P.safety * P.e_m * mt_b, &hu);
+        if (hu) return out;
+        out.bin = bin;
+        out.reco = make_float4(mt_b, mw_b, pz, met);
+    }
+    out.f = f;
+    return out;
+}
+
+}  // namespace hf
