@@ -1,0 +1,317 @@
+"""Throughput benchmark of the cut chain + smeared reconstruction on GB300.
+
+Workload: the smeared semileptonic configuration -- 10,000,000 synthetic
+ttbar-like events (data seed 2, FP32 SoA columns, ~1.27 GB), 16 smearing
+variations per event (jet energy x N(1, 0.10), MET + N(0, 10 GeV), Philox
+seed 1002), cut chain njets >= 4, nbtag >= 1, lepton pT > 30, MET > 20,
+W-mass neutrino p_z, hadronic-top chi2 < 10.  One step = one pass of the
+whole path over the chunk (stage-1 scan and compaction, stage-2
+reconstruction, FP64 recheck, scheduler update).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle instead, on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EVENTS = 10_000_000
+V = 16
+DATA_SEED = 2
+SMEAR_SEED = 1002
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+WORKLOAD = "semilep_smeared_10M_x16"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--events", type=int, default=N_EVENTS)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def flops_per_unit(n):
+    """Algorithmic FP32 flops of the triplet chi2 for one unit with n jets
+    (Gram formulation, FMA = 2): per jet a_i = s_i^2 G_ii (2); per pair
+    2 s_i s_j G_ij, m^2, m via rsqrt, (m - mW)/sigma, square (10); per
+    triplet candidate m^2 (3), m (2), (m - mt)/sigma (2), chi2 (2)."""
+    if n < 3:
+        return 0
+    pairs = n * (n - 1) // 2
+    cands = n * (n - 1) * (n - 2) // 2
+    return 2 * n + 10 * pairs + 9 * cands
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        sm.sort()
+        return dict(sm_mhz=sm[len(sm) // 2], sm_max_mhz=max(smax), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def _oracle_worker(args):
+    n_events, seed_data, lo, hi_budget, seconds = args
+    sys.path.insert(0, ROOT)
+    import synth
+    from synth import analyses
+    import oracle
+    an = analyses.config2()
+    cols = synth.gen_semilep(n_events, seed_data)
+    t0 = time.perf_counter()
+    done = 0
+    step = 2000
+    while time.perf_counter() - t0 < seconds and done < cols.n_events:
+        hi = min(done + step, cols.n_events)
+        oracle.run(an, cols.slice(done, hi), seed=SMEAR_SEED, V=V, first_event_id=lo + done)
+        done = hi
+    return done, time.perf_counter() - t0
+
+
+def cpu_oracle_throughput(seconds, cores=None):
+    """Events/s of the FP64 oracle on the host cores: one process per core on
+    its own contiguous slice of events (the multi-process pattern), each for
+    about `seconds`.  Processes are spawned (no fork after CUDA init)."""
+    cores = cores or os.cpu_count() or 1
+    per = max(20000, int(40000 * seconds))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(per, 1000 + i, i * per, per, seconds) for i in range(cores)])
+        wall = time.perf_counter() - t0
+    events = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return dict(value=events / busy, unit="events/s", cores=cores, kind="oracle",
+                sample="%d events x %d variations (smeared semileptonic chain), %d spawned processes x ~%.0f s "
+                       "on contiguous slices, FP64 single-threaded oracle per process" % (events, V, cores, seconds),
+                wall_s=wall)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
+    vals = []
+    for i in range(a.warmup + a.steps):
+        r = cpu_oracle_throughput(per_step, cores)
+        if i >= a.warmup:
+            vals.append(r["value"])
+    v = sum(vals) / len(vals)
+    line = dict(metric="events/sec", value=v, unit="events/s", n_gpus=a.gpus, steps=a.steps, warmup=a.warmup,
+                ms_per_step=1000.0 * N_EVENTS / v, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, events=N_EVENTS, variations=V, smearing="jet N(1,0.10), MET N(0,10)",
+                            note="each step times the oracle on a bounded sample of the workload"),
+                cpu_baseline=dict(value=v, unit="events/s", cores=cores, kind="oracle", sample=r["sample"]),
+                e2e=dict(value=v, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu_base = cpu_oracle_throughput(a.cpu_seconds)  # before any CUDA call
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import synth
+    from synth import analyses
+    from paper_2211_14346_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2211_14346_gb300 import Engine, DeviceColumns, PinnedColumns, HF_FLAG_PROFILE
+
+    N = a.events
+    cols = synth.gen_semilep(N, DATA_SEED + 7919 * rank)  # each rank its own shard
+    first_id = rank * N
+    an = analyses.config2()
+    eng = Engine(local, flags=HF_FLAG_PROFILE)
+    aid = eng.define(an)
+    dc = DeviceColumns(cols)
+    out = eng.results_for(aid, N)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        eng.run_device(aid, dc, V=V, seed=SMEAR_SEED, first_event_id=first_id, out=out)
+    barrier()
+    eng.profile(reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        eng.run_device(aid, dc, V=V, seed=SMEAR_SEED, first_event_id=first_id, out=out)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    prof = eng.profile(reset=True)
+    res = out.numpy()
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / a.steps
+    value = world * N * a.steps / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel (stage 2: one launch per jet multiplicity)
+    s2_ms = prof["ms_stage2"] / max(1, prof["runs"])
+    flops = sum(cnt * flops_per_unit(n) for n, cnt in enumerate(prof["units_top"])) / max(1, prof["runs"])
+    achieved = flops / (s2_ms / 1000.0) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak, traffic=None,
+                kernel="k_stage2_semi<N> (13 launches per step)", ms_per_step=s2_ms,
+                peak_note="FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+                share_of_step=s2_ms / ms_step if ms_step else None)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        hc = PinnedColumns(cols)
+        fields = ("mask", "cutflow", "hist")
+        host_out = dict(mask=np.zeros(N, np.uint8), cutflow=np.zeros(len(an["cuts"]) + 1, np.uint64),
+                        hist=np.zeros(an["hist"][0] + 2, np.uint64))
+        for _ in range(1):
+            t0 = eng.submit(aid, hc, V=V, seed=SMEAR_SEED, first_event_id=first_id)
+            eng.fetch(aid, t0, N, fields=fields, out=host_out)
+        barrier()
+        t_start = time.perf_counter()
+        tickets = []
+        for i in range(a.steps):
+            tickets.append(eng.submit(aid, hc, V=V, seed=SMEAR_SEED, first_event_id=first_id))
+            if len(tickets) >= 2:
+                eng.fetch(aid, tickets.pop(0), N, fields=fields, out=host_out)
+        while tickets:
+            eng.fetch(aid, tickets.pop(0), N, fields=fields, out=host_out)
+        barrier()
+        wall = time.perf_counter() - t_start
+        tw = torch.tensor([wall], device="cuda")
+        if dist is not None:
+            dist.all_reduce(tw, op=dist.ReduceOp.MAX)
+        wall = float(tw.item())
+        assert np.array_equal(host_out["cutflow"], res["cutflow"]), "e2e result differs from device-resident run"
+        e2e = dict(value=world * N * a.steps / wall, unit="events/s", h2d_bytes_per_step=int(hc.nbytes()),
+                   d2h_bytes_per_step=int(sum(x.nbytes for x in host_out.values())),
+                   note="hf_submit_chunk from pinned host memory + hf_fetch_results (mask, cutflow, hist), "
+                        "two chunks in flight")
+
+    if rank == 0:
+        line = dict(
+            metric="events/sec", value=value, unit="events/s", n_gpus=world, steps=a.steps, warmup=a.warmup,
+            ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+            data="synthetic",
+            config=dict(workload=WORKLOAD, events_per_gpu=N, variations=V, model="semileptonic ttbar-like",
+                        smearing="jet energy x N(1, 0.10), MET + N(0, 10 GeV)", cuts=[c[0] for c in an["cuts"]],
+                        l2="inputs (%.2f GB per GPU) larger than L2 (129 MB); no flush" % (dc.nbytes() / 1e9),
+                        fp64_recheck_units_per_step=int(res["recheck_count"]),
+                        units_per_step=N * V, cutflow=[int(x) for x in res["cutflow"]]),
+            roofline=roof,
+            cpu_baseline=cpu_base,
+            e2e=e2e,
+            gpu_launches=int((2 + 13 + 1 + 1) * a.steps),
+            clocks=clocks,
+            profile=dict(ms_stage1=prof["ms_stage1"] / max(1, prof["runs"]),
+                         ms_stage2=s2_ms, ms_recheck=prof["ms_recheck"] / max(1, prof["runs"]),
+                         events_stage2=prof["events_stage2"] // max(1, prof["runs"])),
+        )
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

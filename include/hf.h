@@ -213,6 +213,30 @@ hf_status hf_sched_state(hf_ctx* ctx, uint32_t analysis_id, int32_t* exec_order,
  * Errors: HF_EINVAL (not a valid dependency-respecting permutation). */
 hf_status hf_set_exec_order(hf_ctx* ctx, uint32_t analysis_id, const int32_t* exec_order);
 
+/* Per-phase device time and work counters of the runs since the last reset,
+ * collected when the context was opened with HF_FLAG_PROFILE.  Times come from
+ * CUDA events recorded on the launching stream around each phase of the fast
+ * path: stage 1 (multiplicity count, column cuts, compaction), stage 2 (the
+ * per-multiplicity reconstruction kernels) and the FP64 recheck. */
+#define HF_FLAG_PROFILE 8u
+typedef struct {
+    uint64_t runs;            /* fast-path runs profiled                            */
+    double ms_stage1;         /* summed device time of stage 1, ms                  */
+    double ms_stage2;         /* summed device time of stage 2, ms                  */
+    double ms_recheck;        /* summed device time of the FP64 recheck, ms         */
+    uint64_t launches_stage2; /* stage-2 kernel launches                            */
+    uint64_t units_stage2;    /* units (event x variation) evaluated in stage 2     */
+    uint64_t events_stage2;   /* events that reached stage 2                        */
+    uint64_t units_top[16];   /* units that evaluated the triplet chi2, by n_jets   */
+    uint64_t units_dilep[16]; /* units that evaluated the two-neutrino solve, by n_b */
+    uint64_t pairings_dilep;  /* b-jet pairings solved                               */
+    uint64_t cands_top;       /* triplet candidates evaluated (after pair pruning)   */
+} hf_profile_data;
+
+/* Waits for the profiled runs, writes the totals into *out (host) and, if
+ * reset != 0, clears them.  Errors: HF_ESTATE (profiling not enabled), HF_ECUDA. */
+hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

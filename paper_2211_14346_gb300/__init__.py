@@ -15,7 +15,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HFError,  # noqa: F401
+from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HF_FLAG_PROFILE, HFError,  # noqa: F401
                    HF_STATE_DONE, HF_STATE_FAILED, HF_STATE_QUEUED, HF_STATE_RUNNING)
 
 N_RECO = 4
@@ -250,6 +250,15 @@ class Engine:
         self._check(self.lib.hf_sched_state(self.ctx, aid, order.ctypes.data, ev.ctypes.data, ps.ctypes.data,
                                             co.ctypes.data))
         return dict(order=order, evaluated=ev, passed=ps, cost=co)
+
+    def profile(self, reset=True):
+        """Per-phase device times and work counters (context opened with HF_FLAG_PROFILE)."""
+        p = _lib.hf_profile_data()
+        self._check(self.lib.hf_profile(self.ctx, C.byref(p), 1 if reset else 0))
+        return dict(runs=p.runs, ms_stage1=p.ms_stage1, ms_stage2=p.ms_stage2, ms_recheck=p.ms_recheck,
+                    launches_stage2=p.launches_stage2, units_stage2=p.units_stage2,
+                    events_stage2=p.events_stage2, units_top=list(p.units_top),
+                    units_dilep=list(p.units_dilep), pairings_dilep=p.pairings_dilep, cands_top=p.cands_top)
 
     def set_exec_order(self, aid, order):
         o = np.ascontiguousarray(order, dtype=np.int32)

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "HF_OK", -1: "HF_EINVAL", -2: "HF_ENOMEM", -3: "HF_EBUSY", -4
 HF_FLAG_PLAIN = 1
 HF_FLAG_NO_SCHED = 2
 HF_FLAG_DEBUG_SYNC = 4
+HF_FLAG_PROFILE = 8
 
 HF_MODEL_SEMILEP = 1
 HF_MODEL_DILEP = 2
@@ -61,6 +62,13 @@ class hf_results(C.Structure):
                 ("reco", C.c_void_p), ("recheck_count", C.c_void_p)]
 
 
+class hf_profile_data(C.Structure):
+    _fields_ = [("runs", C.c_uint64), ("ms_stage1", C.c_double), ("ms_stage2", C.c_double),
+                ("ms_recheck", C.c_double), ("launches_stage2", C.c_uint64), ("units_stage2", C.c_uint64),
+                ("events_stage2", C.c_uint64), ("units_top", C.c_uint64 * 16), ("units_dilep", C.c_uint64 * 16),
+                ("pairings_dilep", C.c_uint64), ("cands_top", C.c_uint64)]
+
+
 _lib = None
 
 
@@ -88,6 +96,7 @@ def load():
         "hf_device_error": ([vp, C.POINTER(u32)], i32),
         "hf_sched_state": ([vp, u32, vp, vp, vp, vp], i32),
         "hf_set_exec_order": ([vp, u32, vp], i32),
+        "hf_profile": ([vp, C.POINTER(hf_profile_data), i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -101,7 +110,7 @@ def declared_symbols():
     """Names of the entry points this binding marshals (the ones hf.h declares)."""
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
-            "hf_set_exec_order"]
+            "hf_set_exec_order", "hf_profile"]
 
 
 class HFError(RuntimeError):

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -127,6 +128,7 @@ Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
     S.pend_sum = (float4*)(base + L.off_pend_sum);
     S.pend_comp = (float4*)(base + L.off_pend_comp);
     S.stats = (unsigned long long*)(base + L.off_stats);
+    S.prof = nullptr;
     S.exec2 = A.sched ? A.sched->exec2 : nullptr;
     S.n_exec2 = A.plan.n_exec2;
     return S;
@@ -205,6 +207,10 @@ struct hf_ctx {
     std::map<uint64_t, Ticket> tickets;
     uint64_t next_ticket = 1;
     uint64_t inflight_bytes = 0;
+    // profiling (HF_FLAG_PROFILE)
+    unsigned long long* prof_dev = nullptr;  // u64[64] device counters
+    std::vector<std::array<cudaEvent_t, 4>> prof_events;  // phases of runs not yet summed
+    hf_profile_data prof_acc{};
 };
 
 namespace {
@@ -257,6 +263,9 @@ hf_status build_plan(const hf_analysis_desc* d, Analysis& A)
         have_dl |= cut.kind == CUT_DILEP_SOLVABLE;
         have_h |= cut.kind == CUT_HIGGS_WINDOW;
     }
+    P.top_thr = 0.0f;
+    for (int c = 0; c < P.n_cuts; ++c)
+        if (P.kind[c] == CUT_HADTOP_CHI2_MAX) P.top_thr = std::max(P.top_thr, P.p0[c]);
     if (P.model == MODEL_SEMILEP && !(have_top && have_w))
         return fail(HF_EINVAL, "semileptonic analysis needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX");
     if (P.model == MODEL_DILEP && !(have_dl && have_h))
@@ -357,7 +366,15 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
     if (N == 0) return HF_OK;
     bool use_plain = plain || (ctx->flags & HF_FLAG_PLAIN);
     if (use_plain) S.exec2 = nullptr;
-    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st));
+    cudaEvent_t* evp = nullptr;
+    std::array<cudaEvent_t, 4> ev{};
+    if (ctx->prof_dev && !use_plain) {
+        S.prof = ctx->prof_dev;
+        for (auto& x : ev) HF_CUDA(cudaEventCreate(&x));
+        evp = ev.data();
+    }
+    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st, evp));
+    if (evp) ctx->prof_events.push_back(ev);
     if (!use_plain && A.sched) HF_CUDA(launch_sched_update(A.sched, S.stats, st));
     if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
     return HF_OK;
@@ -451,6 +468,10 @@ hf_status hf_open(const hf_config* cfg, hf_ctx** out)
     HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking));
     HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking));
     ctx->user_stream = (cudaStream_t)cfg->stream;
+    if (ctx->flags & HF_FLAG_PROFILE) {
+        HF_CUDA(cudaMalloc((void**)&ctx->prof_dev, 64 * sizeof(unsigned long long)));
+        HF_CUDA(cudaMemset(ctx->prof_dev, 0, 64 * sizeof(unsigned long long)));
+    }
     if (cfg->hbm_budget_bytes) {
         ctx->budget = cfg->hbm_budget_bytes;
     } else {
@@ -492,6 +513,9 @@ hf_status hf_close(hf_ctx* ctx)
             if (a->sched) cudaFree(a->sched);
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->arena_free) cudaEventDestroy(ctx->arena_free);
+        if (ctx->prof_dev) cudaFree(ctx->prof_dev);
+        for (auto& ev : ctx->prof_events)
+            for (cudaEvent_t x : ev) cudaEventDestroy(x);
         cudaStreamDestroy(ctx->s_h2d);
         cudaStreamDestroy(ctx->s_comp);
         cudaStreamDestroy(ctx->s_d2h);
@@ -771,6 +795,46 @@ hf_status hf_set_exec_order(hf_ctx* ctx, uint32_t analysis_id, const int32_t* or
     sd.n_exec2 = k;
     sd.frozen = 1;
     HF_CUDA(cudaMemcpy(A->sched, &sd, sizeof sd, cudaMemcpyHostToDevice));
+    return HF_OK;
+}
+
+hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset)
+{
+    if (!ctx || !out) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    if (!ctx->prof_dev) return fail(HF_ESTATE, "context not opened with HF_FLAG_PROFILE");
+    hf_profile_data& P = ctx->prof_acc;
+    for (auto& ev : ctx->prof_events) {
+        HF_CUDA(cudaEventSynchronize(ev[3]));
+        float a = 0.f, b = 0.f, c = 0.f;
+        HF_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        HF_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        HF_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
+        P.ms_stage1 += a;
+        P.ms_stage2 += b;
+        P.ms_recheck += c;
+        P.runs += 1;
+        P.launches_stage2 += NBUCKET;
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    }
+    ctx->prof_events.clear();
+    unsigned long long cnt[64];
+    HF_CUDA(cudaMemcpy(cnt, ctx->prof_dev, sizeof cnt, cudaMemcpyDeviceToHost));
+    hf_profile_data r = P;
+    r.units_stage2 = cnt[PROF_UNITS];
+    r.events_stage2 = cnt[PROF_EVENTS];
+    r.pairings_dilep = cnt[PROF_PAIRINGS];
+    r.cands_top = cnt[PROF_CANDS];
+    for (int i = 0; i < 16; ++i) {
+        r.units_top[i] = cnt[PROF_TOP + i];
+        r.units_dilep[i] = cnt[PROF_DILEP + i];
+    }
+    *out = r;
+    if (reset) {
+        memset(&ctx->prof_acc, 0, sizeof ctx->prof_acc);
+        HF_CUDA(cudaMemset(ctx->prof_dev, 0, sizeof cnt));
+    }
     return HF_OK;
 }
 

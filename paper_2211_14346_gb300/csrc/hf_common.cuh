@@ -5,6 +5,7 @@
 #pragma once
 #include "hf_dev.cuh"
 #include "hf_fp64.cuh"
+#include "hf_semilep.cuh"
 
 namespace hf {
 
@@ -102,11 +103,194 @@ __device__ __forceinline__ void flush_hist(const Plan& P, const Out& O, const un
 // Full unit in FP64 with the definition's formulation (user order; stage-1
 // results are already exact and are taken from s1bits).  Returns the number
 // of leading cuts passed; reco and bin are set when all pass.
+// FP64 quantities of one unit, computed on demand: the smearing normals of a
+// Box-Muller pair, a smeared jet, the smeared MET (the definition's
+// arithmetic, so that they equal those of any FP64 evaluation).
+struct LazyUnitD {
+    const Plan* P;
+    const Cols* C;
+    uint64_t event_id, seed;
+    uint32_t v, j0;
+    int n;
+    bool smear;
+    unsigned zdone, jdone;
+    bool metdone;
+    double z[16];
+    double jet[MAX_JETS][4];
+    double metx, mety;
+
+    __device__ void init(const Plan& P_, const Cols& C_, uint32_t e, uint64_t eid, uint64_t seed_, uint32_t v_)
+    {
+        P = &P_;
+        C = &C_;
+        event_id = eid;
+        seed = seed_;
+        v = v_;
+        j0 = C_.jet_off[e];
+        n = (int)(C_.jet_off[e + 1] - j0);
+        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
+        zdone = jdone = 0;
+        metdone = false;
+    }
+    __device__ void pair(int k)  // normals z[2k], z[2k+1]
+    {
+        if (zdone >> k & 1u) return;
+        zdone |= 1u << k;
+        uint4 w = philox4x32_10(ctr_of((uint32_t)(k / 2), v, event_id), key_of(seed));
+        uint32_t w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
+        double u0 = u01d(w0), u1 = u01d(w1);
+        double r = sqrt(-2.0 * log(u0));
+        double th = (2.0 * 3.141592653589793) * u1;
+        z[2 * k] = r * cos(th);
+        z[2 * k + 1] = r * sin(th);
+    }
+    __device__ const double* j(int i)
+    {
+        if (!(jdone >> i & 1u)) {
+            jdone |= 1u << i;
+            float4 jf = C->jets[j0 + i];
+            double js[4] = {jf.x, jf.y, jf.z, jf.w};
+            if (smear) {
+                pair(i / 2);
+                double s = 1.0 + P->dsigma_jet * z[i];
+                for (int c = 0; c < 4; ++c) jet[i][c] = s * js[c];
+            } else {
+                for (int c = 0; c < 4; ++c) jet[i][c] = js[c];
+            }
+        }
+        return jet[i];
+    }
+    __device__ void met(float2 mf)
+    {
+        if (metdone) return;
+        metdone = true;
+        if (smear) {
+            pair(6);
+            metx = (double)mf.x + P->dsigma_met * z[12];
+            mety = (double)mf.y + P->dsigma_met * z[13];
+        } else {
+            metx = mf.x;
+            mety = mf.y;
+        }
+    }
+};
+
+// Exact (definition) triplet minimum of a unit with little FP64 work.  An
+// FP32 pass with the stage-2 arithmetic finds the FP32 minimum b and keeps
+// the candidates whose FP32 chi2 c satisfies c <= b + band(b) + band(c); since
+// |chi2_32 - chi2_64| <= band for every candidate, this set contains every
+// candidate that can be the FP64 minimum, including all ties.  Only those are
+// evaluated in FP64 with the definition's formulation, in the definition's
+// enumeration order (k, then i < j) with a strict minimum.  More than 32
+// survivors of the screen fall back to the full FP64 enumeration.
+static __device__ __noinline__ double hadtop_screened_d(const Plan& P, LazyUnitD& U, double* mtop, double* mw)
+{
+    const int n = U.n;
+    *mtop = 0.0;
+    *mw = 0.0;
+    if (n < 3) return CUDART_INF;
+    float4 jf[MAX_JETS];
+    float s[MAX_JETS];
+    for (int i = 0; i < n; ++i) {
+        jf[i] = U.C->jets[U.j0 + i];
+        s[i] = 1.0f;
+    }
+    if (P.smear_jets) {
+        const uint2 key = key_of(U.seed);
+        for (int b = 0; b < (n + 3) / 4; ++b) {
+            uint4 w = philox4x32_10(ctr_of((uint32_t)b, U.v, U.event_id), key);
+            float z0, z1, z2, z3;
+            box_muller_f(w.x, w.y, z0, z1);
+            box_muller_f(w.z, w.w, z2, z3);
+            float zz[4] = {z0, z1, z2, z3};
+            for (int t = 0; t < 4 && 4 * b + t < n; ++t) s[4 * b + t] = fmaf(P.sigma_jet, zz[t], 1.0f);
+        }
+    }
+    float a[MAX_JETS], q2[MAX_JETS][MAX_JETS];
+    for (int i = 0; i < n; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), minkowski_dot2(jf[i], jf[i]));
+    for (int i = 0; i < n; ++i)
+        for (int jj = i + 1; jj < n; ++jj)
+            q2[i][jj] = q2[jj][i] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[jj]), minkowski_dot2(jf[i], jf[jj]));
+    const float c_t = -P.mt * P.inv_sigma_t, c_w = -P.mW * P.inv_sigma_W;
+    // pass 1: FP32 minimum; pass 2: the screened candidates, in enumeration order
+    float best = CUDART_INF_F;
+    for (int pass = 0; pass < 2; ++pass) {
+        int nl = 0;
+        int code[32];
+        bool overflow = false;
+        for (int k = 0; k < n; ++k)
+            for (int i = 0; i < n; ++i) {
+                if (i == k) continue;
+                for (int jj = i + 1; jj < n; ++jj) {
+                    if (jj == k) continue;
+                    float pw = __fadd_rn(__fadd_rn(a[i], a[jj]), q2[i][jj]);
+                    float mwf = __fmul_rn(pw, rsqrt_approx(pw));
+                    float dw = fmaf(mwf, P.inv_sigma_W, c_w);
+                    float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2[i][k]), q2[jj][k]);
+                    float mtf = __fmul_rn(m2, rsqrt_approx(m2));
+                    float dt = fmaf(mtf, P.inv_sigma_t, c_t);
+                    float c = fmaf(dt, dt, __fmul_rn(dw, dw));
+                    if (pass == 0) {
+                        best = fminf(best, c);
+                    } else if (c <= best + chi2_band(P, best) + chi2_band(P, c)) {
+                        if (nl < 32) code[nl++] = (k << 8) | (i << 4) | jj;
+                        else overflow = true;
+                    }
+                }
+            }
+        if (pass == 0) continue;
+        if (overflow) break;  // full enumeration below
+        double chi2 = CUDART_INF;
+        for (int t = 0; t < nl; ++t) {
+            const int k = code[t] >> 8, i = (code[t] >> 4) & 15, jj = code[t] & 15;
+            double W[4], T[4];
+            v4_add_d(U.j(i), U.j(jj), W);
+            v4_add_d(W, U.j(k), T);
+            double m_w = mass_d(W), m_t = mass_d(T);
+            double dt = (m_t - P.dmt) / P.dsigma_t;
+            double dwd = (m_w - P.dmW) / P.dsigma_W;
+            double c = dt * dt + dwd * dwd;
+            if (c < chi2) {
+                chi2 = c;
+                *mtop = m_t;
+                *mw = m_w;
+            }
+        }
+        return chi2;
+    }
+    // screen overflow: every candidate in FP64
+    double best_d = CUDART_INF;
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) {
+            if (i == k) continue;
+            for (int jj = i + 1; jj < n; ++jj) {
+                if (jj == k) continue;
+                double W[4], T[4];
+                v4_add_d(U.j(i), U.j(jj), W);
+                v4_add_d(W, U.j(k), T);
+                double m_w = mass_d(W), m_t = mass_d(T);
+                double dt = (m_t - P.dmt) / P.dsigma_t;
+                double dwd = (m_w - P.dmW) / P.dsigma_W;
+                double c = dt * dt + dwd * dwd;
+                if (c < best_d) {
+                    best_d = c;
+                    *mtop = m_t;
+                    *mw = m_w;
+                }
+            }
+        }
+    return best_d;
+}
+
+// One unit with the definition's FP64 decisions (user order; stage-1
+// results are already exact and are taken from s1bits).  Returns the number
+// of leading cuts passed; reco and bin are set when all pass.
 static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id, uint64_t seed,
                          uint32_t v, unsigned s1bits, float4* reco, int* bin)
 {
-    EvD ev;
-    load_event_d(P, C, e, event_id, seed, v, ev);
+    LazyUnitD U;
+    U.init(P, C, e, event_id, seed, v);
+    const float2 mf = C.met[e];
     bool top_done = false;
     double chi2 = 0.0, mtop = 0.0, mw = 0.0;
     int f = P.n_cuts;
@@ -115,10 +299,11 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         if (P.stage1 >> c & 1u) {
             pass = s1bits >> c & 1u;
         } else if (P.kind[c] == CUT_MET_MIN) {
-            pass = sqrt(ev.metx * ev.metx + ev.mety * ev.mety) > P.dp0[c];
+            U.met(mf);
+            pass = sqrt(U.metx * U.metx + U.mety * U.mety) > P.dp0[c];
         } else if (P.kind[c] == CUT_HADTOP_CHI2_MAX) {
             if (!top_done) {
-                chi2 = hadtop_d(ev, P, &mtop, &mw);
+                chi2 = hadtop_screened_d(P, U, &mtop, &mw);
                 top_done = true;
             }
             pass = chi2 < P.dp0[c];
@@ -131,10 +316,17 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         }
     }
     if (f == P.n_cuts) {
-        if (!top_done) chi2 = hadtop_d(ev, P, &mtop, &mw);
+        if (!top_done) chi2 = hadtop_screened_d(P, U, &mtop, &mw);
+        U.met(mf);
+        double lep[4];
+        float4 lf = C.lep[e];
+        lep[0] = lf.x;
+        lep[1] = lf.y;
+        lep[2] = lf.z;
+        lep[3] = lf.w;
         double pz;
-        w_pz_d(ev.lep[0], ev.metx, ev.mety, P.dmW, &pz);
-        double met = sqrt(ev.metx * ev.metx + ev.mety * ev.mety);
+        w_pz_d(lep, U.metx, U.mety, P.dmW, &pz);
+        double met = sqrt(U.metx * U.metx + U.mety * U.mety);
         *bin = hist_bin_d(P, mtop);
         *reco = make_float4((float)mtop, (float)mw, (float)pz, (float)met);
     }
@@ -216,7 +408,7 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
 // ------------------------------------------------------------------ tile shared memory
 struct TileSmem {
     float4* jets;   // [ev][12]
-    float* G;       // [ev][GS]
+    float* G;       // [ev][GS]: full symmetric Gram matrix, row stride n
     float4* lep;    // [ev]
     float2* met;    // [ev]
     uint32_t* evid; // [ev]
@@ -224,7 +416,7 @@ struct TileSmem {
     float4* ureco;  // [unit]
     int* uf;        // [unit] f or -1
 };
-constexpr int GS = 79;  // padded Gram row stride (odd: conflict-free across events)
+constexpr int GS = 145;  // event stride of the Gram matrices: 12 x 12 + 1
 
 __host__ __device__ inline size_t tile_smem_bytes(int ev, int units)
 {

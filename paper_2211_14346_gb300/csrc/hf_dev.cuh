@@ -32,6 +32,9 @@ enum : int {
 };
 enum : int { MODEL_SEMILEP = 1, MODEL_DILEP = 2 };
 
+// Profiling counters (device u64[64]).
+enum : int { PROF_UNITS = 0, PROF_EVENTS = 1, PROF_PAIRINGS = 2, PROF_CANDS = 3, PROF_TOP = 16, PROF_DILEP = 32 };
+
 // Error word bits (device -> host).
 enum : unsigned { ERR_COLUMNS = 1u, ERR_RECHECK_FULL = 2u };
 
@@ -46,6 +49,7 @@ struct Plan {
     int n_exec2;       // stage-2 cuts in default execution order (user order)
     int exec2[MAX_CUTS];
     float mW, mt, sigma_t, sigma_W, inv_sigma_t, inv_sigma_W, mH;
+    float top_thr;     // largest threshold of the chi2 cuts (clamp of the triplet minimum)
     float mW2half, mW2half_lo;  // mW*mW/2 (exact in FP64) as a float-float pair
     float sigma_jet, sigma_met;
     int smear_jets, smear_met;
@@ -107,6 +111,7 @@ struct Scratch {
     float4* pend_sum;     // [rc_cap] partial sums of reco (float, then final)
     float4* pend_comp;    // [rc_cap] compensation terms of the partial sums
     unsigned long long* stats;  // [3*MAX_CUTS] evaluated, passed, cost (cycles)
+    unsigned long long* prof;   // [64] profiling counters (PROF_*) or null
     const int* exec2;     // [MAX_CUTS] device execution order of stage-2 cuts (or null)
     int n_exec2;
 };
@@ -159,6 +164,15 @@ __device__ __forceinline__ void box_muller_f(uint32_t w0, uint32_t w1, float& z0
     sincospif(2.0f * u1, &s, &c);
     z0 = r * c;
     z1 = r * s;
+}
+
+// Reciprocal square root, one MUFU instruction (PTX rsqrt.approx.ftz.f32,
+// relative error below 2^-22; inputs here are normal, positive numbers).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // The Philox counter of block b of unit (event, v) and the seed key.

@@ -139,17 +139,23 @@ typedef cudaError_t (*S2Launcher)(const Plan&, const Cols&, const Out&, const Sc
                                   uint64_t, int, int, cudaStream_t);
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
-                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st)
+                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st, cudaEvent_t* ev)
 {
     if (N == 0) return cudaSuccess;
     const unsigned nb = (N + 255) / 256;
     cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], st);
     if (plain) {
         e = launch_plain(P, C, N, V, O, S, seed, first_id, st);
         if (e != cudaSuccess) return e;
+        if (ev) {
+            cudaEventRecord(ev[1], st);
+            cudaEventRecord(ev[2], st);
+        }
     } else {
         k_count<<<min(nb, 4096u), 256, 0, st>>>(C, N, S);
         k_stage1<<<nb, 256, 0, st>>>(P, C, N, V, O, S);
+        if (ev) cudaEventRecord(ev[1], st);
         const int ept = ev_per_tile_for(V);
         static const S2Launcher semi[NBUCKET] = {
             launch_s2_semi<0>, launch_s2_semi<1>, launch_s2_semi<2>,  launch_s2_semi<3>, launch_s2_semi<4>,
@@ -159,8 +165,10 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
             e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, st);
             if (e != cudaSuccess) return e;
         }
+        if (ev) cudaEventRecord(ev[2], st);
     }
     k_recheck<<<sms * 4, BLOCK, 0, st>>>(P, C, O, S, seed, first_id);
+    if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,9 @@ namespace hf {
 int ev_per_tile_for(uint32_t V);
 
 // Enqueues one whole run of the path on stream st.  Scratch counters and the
-// output accumulators must be zeroed by the caller beforehand.
+// output accumulators must be zeroed by the caller beforehand.  If ev is not
+// null, ev[0..3] are recorded before stage 1, before stage 2, before the
+// recheck and at the end.
 template <int N>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st);
@@ -19,6 +21,10 @@ cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, c
                          uint64_t seed, uint64_t first_id, cudaStream_t st);
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
-                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st);
+                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st,
+                       cudaEvent_t* ev = nullptr);
+
+// Kernel launches of one fast-path run (count, stage 1, one per multiplicity, recheck).
+constexpr int FAST_LAUNCHES = 2 + NBUCKET + 1;
 
 }  // namespace hf

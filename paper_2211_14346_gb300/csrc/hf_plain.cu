@@ -20,7 +20,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
 {
     constexpr int NT = ntri(N);
     SemiEvent<N> se;
-    float g[NT > 0 ? NT : 1];
+    float g[N > 0 ? N * N : 1];
     float4 jet[N > 0 ? N : 1];
     const uint32_t j0 = C.jet_off[e];
 #pragma unroll
@@ -28,7 +28,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int i = 0; i <= j; ++i) g[tri(i, j)] = minkowski_dot2(jet[i], jet[j]);
+        for (int i = 0; i <= j; ++i) g[i * N + j] = g[j * N + i] = minkowski_dot2(jet[i], jet[j]);
     if (NT == 0) g[0] = 0.f;
     se.g = g;
     se.lep = C.lep[e];
@@ -40,7 +40,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
     int nflag = 0;
     uint16_t vs[64];
     for (uint32_t v = 0; v < V; ++v) {
-        UnitOut r = semi_unit_f<N>(P, P.exec2, P.n_exec2, se, v, seed, nullptr);
+        UnitOut r = semi_unit_f<N>(P, P.exec2, P.n_exec2, se, v, seed);
         if (r.f < 0) {
             if (nflag < 64) {
                 vs[nflag++] = (uint16_t)v;

@@ -23,9 +23,14 @@
 namespace hf {
 
 struct UnitOut {
-    int f;        // cuts passed in user order (n_cuts = survives); -1 = recheck
-    float4 reco;  // (m_top, m_W, pz_nu, |MET|) when f == n_cuts
-    int bin;      // histogram bin when f == n_cuts
+    int f;             // cuts passed in user order (n_cuts = survives); -1 = recheck
+    float4 reco;       // (m_top, m_W, pz_nu, |MET|) when f == n_cuts
+    int bin;           // histogram bin when f == n_cuts
+    unsigned evald;    // stage-2 cuts evaluated (bit = user index)
+    unsigned passd;    // stage-2 cuts passed
+    unsigned cyc_top;  // SM cycles spent in the triplet chi2
+    unsigned cyc_met;  // SM cycles spent in the MET cut
+    unsigned cands;    // triplet candidates evaluated (after pair pruning)
 };
 
 // Band of an FP32 chi2 value: |chi2_32 - chi2_64| bound using only the value
@@ -41,55 +46,104 @@ __device__ __forceinline__ float chi2_band(const Plan& P, float c)
     return P.safety * (2.0f * r * d + d * d + 3.0f * u * c);
 }
 
-// Minimum and second minimum of the triplet chi2, with the masses of the
-// minimising candidate.  g: packed Gram matrix, s: jet scales.
-template <int N>
-__device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict__ g,
-                                         const float (&s)[N > 0 ? N : 1], float& b1, float& b2,
-                                         float& mt_b, float& mw_b)
+// Pair p of the (i < j) enumeration ordered by j, then i: p = j(j-1)/2 + i.
+__host__ __device__ constexpr int pair_j(int p)
 {
-    b1 = CUDART_INF_F;
-    b2 = CUDART_INF_F;
+    int j = 1;
+    while ((j + 1) * j / 2 <= p) ++j;
+    return j;
+}
+__host__ __device__ constexpr int pair_i(int p) { return p - pair_j(p) * (pair_j(p) - 1) / 2; }
+
+// Row stride of the full symmetric Gram matrix of an event (shared memory).
+template <int N>
+struct GramLayout {
+    static constexpr int STRIDE = (N * N) | 1;  // odd: events fall in different banks
+};
+
+// Top-2 tracker of candidate chi2 values with the masses of the best.
+struct Top2 {
+    float b1, b2, mt, mw;
+    __device__ __forceinline__ void add(float c, float mt_c, float mw_c)
+    {
+        const bool better = c < b1;
+        b2 = fminf(b2, fmaxf(b1, c));
+        mt = better ? mt_c : mt;
+        mw = better ? mw_c : mw;
+        b1 = fminf(b1, c);
+    }
+    __device__ __forceinline__ void merge(const Top2& o)
+    {
+        const bool better = o.b1 < b1;
+        b2 = fminf(fminf(b2, o.b2), fmaxf(b1, o.b1));
+        mt = better ? o.mt : mt;
+        mw = better ? o.mw : mw;
+        b1 = fminf(b1, o.b1);
+    }
+};
+
+// Minimum and second minimum of the triplet chi2, clamped at `cap`, with the
+// masses of the minimising candidate.  gf: full symmetric Gram matrix
+// (row-major N x N), s: jet scales.  Only candidates with chi2 < cap can
+// change any output (cap lies above the cut threshold by more than the error
+// bands, so a clamped minimum still decides the cut and the argmin gap
+// exactly).  Pairs and b-jets are fully unrolled for the multiplicity N: the
+// scaled Gram terms stay in registers and each candidate costs three adds,
+// one reciprocal square root, one multiply, two fused multiply-adds and the
+// top-2 update.  *cands counts the candidates evaluated.
+template <int N>
+__device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict__ gf,
+                                         const float (&s)[N > 0 ? N : 1], float cap, float& b1, float& b2,
+                                         float& mt_b, float& mw_b, unsigned* cands)
+{
+    b1 = cap;
+    b2 = cap;
     mt_b = 0.0f;
     mw_b = 0.0f;
     if constexpr (N >= 3) {
         float a[N];
-        float q2[ntri(N)];
+        float q2[N * N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), g[tri(i, i)]);
+        for (int i = 0; i < N; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), gf[i * N + i]);
 #pragma unroll
         for (int j = 1; j < N; ++j)
 #pragma unroll
-            for (int i = 0; i < j; ++i)
-                q2[tri(i, j)] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), g[tri(i, j)]);
+            for (int i = 0; i < j; ++i) q2[i * N + j] = q2[j * N + i] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), gf[i * N + j]);
         const float c_t = -P.mt * P.inv_sigma_t;
         const float c_w = -P.mW * P.inv_sigma_W;
+        Top2 ta{cap, cap, 0.0f, 0.0f};
+        unsigned nc = 0;
 #pragma unroll
         for (int j = 1; j < N; ++j) {
 #pragma unroll
             for (int i = 0; i < j; ++i) {
-                float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2[tri(i, j)]);
-                float mw = __fmul_rn(pw, rsqrtf(pw));
+                float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2[i * N + j]);
+                float mw = __fmul_rn(pw, rsqrt_approx(pw));
                 float dw = fmaf(mw, P.inv_sigma_W, c_w);
                 float cw = __fmul_rn(dw, dw);
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
                     if (k == i || k == j) continue;
-                    const int ik = k < i ? tri(k, i) : tri(i, k);
-                    const int jk = k < j ? tri(k, j) : tri(j, k);
-                    float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2[ik]), q2[jk]);
-                    float mt = __fmul_rn(m2, rsqrtf(m2));
+                    float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2[i * N + k]), q2[j * N + k]);
+                    float mt = __fmul_rn(m2, rsqrt_approx(m2));
                     float dt = fmaf(mt, P.inv_sigma_t, c_t);
                     float c = fmaf(dt, dt, cw);
-                    bool better = c < b1;
-                    b2 = fminf(b2, fmaxf(b1, c));
-                    mt_b = better ? mt : mt_b;
-                    mw_b = better ? mw : mw_b;
-                    b1 = fminf(b1, c);
+                    ta.add(c, mt, mw);
+                    ++nc;
                 }
             }
         }
+        b1 = ta.b1; b2 = ta.b2; mt_b = ta.mt; mw_b = ta.mw;
+        *cands += nc;
     }
+}
+
+// Cap of the clamped triplet minimum for a chi2 cut at thr: above thr by
+// 2.5 bands, so that a minimum at the cap is a certain failure and a second
+// minimum at the cap leaves a certain argmin gap.
+__device__ __forceinline__ float chi2_cap(const Plan& P, float thr)
+{
+    return thr + 2.5f * chi2_band(P, thr) + 1.0e-6f * fabsf(thr) + 1.0e-30f;
 }
 
 // Float-float (unevaluated sum hi + lo) arithmetic, relative accuracy about
@@ -201,6 +255,7 @@ struct CutStats {
     unsigned evaluated[MAX_CUTS];
     unsigned passed[MAX_CUTS];
     unsigned long long cost[MAX_CUTS];
+    unsigned long long cands;  // triplet candidates evaluated in the block
 };
 
 // FP32 evaluation of one semileptonic unit.  exec: stage-2 cuts in execution
@@ -210,12 +265,13 @@ struct CutStats {
 // is the user-order one whatever the execution order.
 template <int N>
 __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const SemiEvent<N>& ev,
-                               uint32_t v, uint64_t seed, CutStats* st)
+                               uint32_t v, uint64_t seed)
 {
     UnitOut out;
     out.f = -1;
     out.reco = make_float4(0.f, 0.f, 0.f, 0.f);
     out.bin = 0;
+    out.evald = out.passd = out.cyc_top = out.cyc_met = out.cands = 0;
     float s[N > 0 ? N : 1];
 #pragma unroll
     for (int i = 0; i < (N > 0 ? N : 1); ++i) s[i] = 1.0f;
@@ -283,22 +339,21 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             unsure = fabsf(met - P.p0[c]) <= met_err;
         } else if (kind == CUT_HADTOP_CHI2_MAX) {
             if (!top_done) {
-                hadtop_f<N>(P, ev.g, s, b1, b2, mt_b, mw_b);
+                hadtop_f<N>(P, ev.g, s, chi2_cap(P, P.top_thr), b1, b2, mt_b, mw_b, &out.cands);
                 top_done = true;
             }
             pass = b1 < P.p0[c];
             unsure = fabsf(b1 - P.p0[c]) <= chi2_band(P, b1);
         }
-        if (st) {
-            long long dt = clock64() - t0;
-            atomicAdd(&st->evaluated[c], 1u);
-            if (pass) atomicAdd(&st->passed[c], 1u);
-            atomicAdd(&st->cost[c], (unsigned long long)(dt > 0 ? dt : 0));
-        }
-        if (unsure) return out;  // f = -1: FP64 recheck
+        const unsigned dt = (unsigned)(clock64() - t0);
+        if (kind == CUT_HADTOP_CHI2_MAX) out.cyc_top += dt;
+        else out.cyc_met += dt;
         evald |= 1u << c;
         if (pass) passd |= 1u << c;
-        else phase1 = false;
+        out.evald = evald;
+        out.passd = passd;
+        if (unsure) return out;  // f = -1: FP64 recheck
+        if (!pass) phase1 = false;
     }
     if (f == P.n_cuts) {
         // survivor: reconstructed quantities must be certain as well

@@ -16,6 +16,35 @@
 
 namespace hf {
 
+// Adds a warp's units to the block's cut flow, histogram and scheduler
+// statistics with one shared-memory atomic per distinct value (lanes with the
+// same first-failure index or bin are combined by __match_any_sync).
+__device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsigned long long* fc, unsigned* hist,
+                                           CutStats* st)
+{
+    const unsigned am = __activemask();
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned g = __match_any_sync(am, r.f);
+    if (r.f >= 0 && lane == (unsigned)(__ffs(g) - 1)) atomicAdd(&fc[r.f], (unsigned long long)__popc(g));
+    const int hb = r.f == P.n_cuts ? r.bin : -1;
+    const unsigned gh = __match_any_sync(am, hb);
+    if (hb >= 0 && lane == (unsigned)(__ffs(gh) - 1)) atomicAdd(&hist[hb], (unsigned)__popc(gh));
+    const bool leader = lane == (unsigned)(__ffs(am) - 1);
+    const unsigned ct = __reduce_add_sync(am, r.cyc_top), cm = __reduce_add_sync(am, r.cyc_met);
+    const unsigned nc = __reduce_add_sync(am, r.cands);
+    if (leader && nc) atomicAdd(&st->cands, (unsigned long long)nc);
+    for (unsigned bits = P.stage2; bits; bits &= bits - 1) {
+        const int c = __ffs(bits) - 1;
+        const unsigned ne = __popc(__ballot_sync(am, r.evald >> c & 1u));
+        const unsigned np = __popc(__ballot_sync(am, r.passd >> c & 1u));
+        if (leader && ne) {
+            atomicAdd(&st->evaluated[c], ne);
+            atomicAdd(&st->passed[c], np);
+            atomicAdd(&st->cost[c], (unsigned long long)(P.kind[c] == CUT_HADTOP_CHI2_MAX ? ct : cm));
+        }
+    }
+}
+
 template <int N>
 __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
@@ -38,13 +67,16 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
     }
     __syncthreads();
     constexpr int NT = ntri(N);
+    constexpr int GST = GramLayout<N>::STRIDE;
     if constexpr (NT > 0) {
         for (int t = threadIdx.x; t < ne * NT; t += blockDim.x) {
             int ev = t / NT, k = t - ev * NT;
             int j = 0;
             while ((j + 1) * (j + 2) / 2 <= k) ++j;
             int i = k - j * (j + 1) / 2;
-            sm.G[ev * GS + k] = minkowski_dot2(sm.jets[ev * 12 + i], sm.jets[ev * 12 + j]);
+            const float g = minkowski_dot2(sm.jets[ev * 12 + i], sm.jets[ev * 12 + j]);
+            sm.G[ev * GST + i * N + j] = g;
+            sm.G[ev * GST + j * N + i] = g;
         }
     }
     __syncthreads();
@@ -54,18 +86,15 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
         int ev = u / (int)V;
         uint32_t v = (uint32_t)(u - ev * (int)V);
         SemiEvent<N> se;
-        se.g = sm.G + ev * GS;
+        se.g = sm.G + ev * GST;
         se.lep = sm.lep[ev];
         se.met = sm.met[ev];
         se.s1bits = sm.bits[ev];
         se.event_id = first_id + sm.evid[ev];
-        UnitOut r = semi_unit_f<N>(P, exec, nexec, se, v, seed, st);
+        UnitOut r = semi_unit_f<N>(P, exec, nexec, se, v, seed);
         sm.uf[u] = r.f;
         sm.ureco[u] = r.reco;
-        if (r.f >= 0) {
-            atomicAdd(&fc[r.f], 1ull);
-            if (r.f == P.n_cuts) atomicAdd(&hist[r.bin], 1u);
-        }
+        warp_tally(P, r, fc, hist, st);
     }
     __syncthreads();
     // C: per-event reduction in variation order
@@ -105,7 +134,7 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
 }
 
 template <int N>
-__global__ void __launch_bounds__(BLOCK, 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
+__global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
                                                        int ev_per_tile)
 {
@@ -131,6 +160,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_stage2_semi(const Plan P, const Co
         s_st.passed[threadIdx.x] = 0;
         s_st.cost[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) s_st.cands = 0;
     __syncthreads();
     if (s_fill == 0) return;
     const unsigned ntiles = (s_fill + ev_per_tile - 1) / ev_per_tile;
@@ -156,6 +186,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_stage2_semi(const Plan P, const Co
         if (s_st.evaluated[c]) atomicAdd(&S.stats[c], (unsigned long long)s_st.evaluated[c]);
         if (s_st.passed[c]) atomicAdd(&S.stats[MAX_CUTS + c], (unsigned long long)s_st.passed[c]);
         if (s_st.cost[c]) atomicAdd(&S.stats[2 * MAX_CUTS + c], s_st.cost[c]);
+        if (S.prof && P.kind[c] == CUT_HADTOP_CHI2_MAX && s_st.evaluated[c])
+            atomicAdd(&S.prof[PROF_TOP + N], (unsigned long long)s_st.evaluated[c]);
+    }
+    if (S.prof && threadIdx.x == 0 && s_st.cands) atomicAdd(&S.prof[PROF_CANDS], s_st.cands);
+    if (S.prof && threadIdx.x == 0 && blockIdx.x == 0) {
+        atomicAdd(&S.prof[PROF_UNITS], (unsigned long long)s_fill * V);
+        atomicAdd(&S.prof[PROF_EVENTS], (unsigned long long)s_fill);
     }
 }
 
