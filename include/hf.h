@@ -237,6 +237,35 @@ typedef struct {
  * reset != 0, clears them.  Errors: HF_ESTATE (profiling not enabled), HF_ECUDA. */
 hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free run.                                                 */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart of this entry point: it serves callers that
+ * cannot allocate device memory when they run a chunk -- code inside a CUDA
+ * stream capture, plug-ins of frameworks that own every device allocation,
+ * real-time loops that must not allocate.  It runs the same path as
+ * hf_run_device (same results; cuts executed in user order, no scheduler)
+ * without a context and without allocating: no cudaMalloc, cudaFree or other
+ * allocating call.  Its scratch memory is one static device array of
+ * HF_NOALLOC_SCRATCH_BYTES in the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - desc, dev_cols, dev_out, stream: as for hf_define_cuts and
+ *     hf_run_device (DEVICE column and result buffers, caller-owned; NULL
+ *     result fields are skipped; stream NULL = the legacy default stream).
+ *   - n_events <= HF_NOALLOC_MAX_EVENTS, else HF_EINVAL with a message.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (current device at the call); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and clears its counters at the start;
+ *     calls whose work overlaps on the GPU (different streams, or several
+ *     host threads without ordering) race and give wrong results: order them.
+ * Errors: HF_EINVAL, HF_ECUDA. */
+#define HF_NOALLOC_MAX_EVENTS 1048576u
+#define HF_NOALLOC_SCRATCH_BYTES 12067840u
+hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const hf_columns* dev_cols, uint64_t n_events,
+                                uint64_t first_event_id, uint64_t seed, uint32_t n_variations,
+                                const hf_results* dev_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,8 @@ def load():
         "hf_sched_state": ([vp, u32, vp, vp, vp, vp], i32),
         "hf_set_exec_order": ([vp, u32, vp], i32),
         "hf_profile": ([vp, C.POINTER(hf_profile_data), i32], i32),
+        "hf_run_device_noalloc": ([C.POINTER(hf_analysis_desc), C.POINTER(hf_columns), u64, u64, u64, u32,
+                                   C.POINTER(hf_results), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -110,7 +112,7 @@ def declared_symbols():
     """Names of the entry points this binding marshals (the ones hf.h declares)."""
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
-            "hf_set_exec_order", "hf_profile"]
+            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc"]
 
 
 class HFError(RuntimeError):

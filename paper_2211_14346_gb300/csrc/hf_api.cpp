@@ -31,21 +31,29 @@
 
 using namespace hf;
 
+// Message of the last error of the calling thread (fixed storage: reporting
+// an error allocates nothing).
 namespace {
+thread_local char g_err[512] = "";
+}  // namespace
 
-thread_local std::string g_err = "";
-
-hf_status fail(hf_status s, const std::string& msg)
+namespace hf {
+hf_status set_error(hf_status s, const char* msg)
 {
-    g_err = msg;
+    snprintf(g_err, sizeof g_err, "%s", msg);
     return s;
 }
-
-hf_status cuda_fail(cudaError_t e, const char* what)
+hf_status set_cuda_error(cudaError_t e, const char* what)
 {
-    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
     return HF_ECUDA;
 }
+}  // namespace hf
+
+namespace {
+
+hf_status fail(hf_status s, const char* msg) { return hf::set_error(s, msg); }
+hf_status cuda_fail(cudaError_t e, const char* what) { return hf::set_cuda_error(e, what); }
 
 #define HF_CUDA(call)                                      \
     do {                                                   \
@@ -224,7 +232,10 @@ hf_status use_device(hf_ctx* ctx)
 
 bool known_kind(int k) { return k >= CUT_NJETS_MIN && k <= CUT_HIGGS_WINDOW; }
 
-hf_status build_plan(const hf_analysis_desc* d, Analysis& A)
+}  // namespace
+
+// Validates a descriptor and fills the kernel plan (no allocation).
+hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
 {
     if (!d) return fail(HF_EINVAL, "desc is NULL");
     if (d->event_model != MODEL_SEMILEP && d->event_model != MODEL_DILEP)
@@ -237,12 +248,10 @@ hf_status build_plan(const hf_analysis_desc* d, Analysis& A)
     if (!(d->sigma_met >= 0.0f) || !std::isfinite(d->sigma_met)) return fail(HF_EINVAL, "sigma_met must be >= 0");
     if (d->hist_nbins < 1 || d->hist_nbins > (uint32_t)MAX_BINS || !(d->hist_lo < d->hist_hi))
         return fail(HF_EINVAL, "histogram: 1..1024 bins and lo < hi");
-    Plan& P = A.plan;
     memset(&P, 0, sizeof P);
     P.model = d->event_model;
     P.n_cuts = (int)d->n_cuts;
     bool have_top = false, have_w = false, have_dl = false, have_h = false;
-    A.cuts.assign(d->cuts, d->cuts + d->n_cuts);
     for (int c = 0; c < P.n_cuts; ++c) {
         const hf_cut& cut = d->cuts[c];
         if (!known_kind(cut.kind)) return fail(HF_EINVAL, "unknown cut kind");
@@ -326,6 +335,8 @@ hf_status build_plan(const hf_analysis_desc* d, Analysis& A)
         if (P.stage2 >> c & 1u) P.exec2[P.n_exec2++] = c;
     return HF_OK;
 }
+
+namespace {
 
 hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
 {
@@ -445,7 +456,7 @@ hf_status run_device_impl(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* d
 
 extern "C" {
 
-const char* hf_last_error(hf_ctx*) { return g_err.c_str(); }
+const char* hf_last_error(hf_ctx*) { return g_err; }
 
 hf_status hf_open(const hf_config* cfg, hf_ctx** out)
 {
@@ -530,7 +541,8 @@ hf_status hf_define_cuts(hf_ctx* ctx, const hf_analysis_desc* desc, uint32_t* an
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (hf_status s = use_device(ctx)) return s;
     std::unique_ptr<Analysis> A(new Analysis);
-    if (hf_status s = build_plan(desc, *A)) return s;
+    if (hf_status s = hf::build_plan(desc, A->plan)) return s;
+    A->cuts.assign(desc->cuts, desc->cuts + desc->n_cuts);
     A->no_sched = (ctx->flags & HF_FLAG_NO_SCHED) != 0;
     SchedDev sd;
     memset(&sd, 0, sizeof sd);

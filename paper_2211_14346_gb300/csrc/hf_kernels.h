@@ -4,7 +4,15 @@
 
 #include "hf_dev.cuh"
 
+#include "hf.h"
+
 namespace hf {
+
+// Validates an analysis descriptor and fills the kernel plan (no allocation).
+hf_status build_plan(const hf_analysis_desc* d, Plan& P);
+// Records the calling thread's error message (fixed storage) and returns s.
+hf_status set_error(hf_status s, const char* msg);
+hf_status set_cuda_error(cudaError_t e, const char* what);
 
 // Events per tile of the stage-2 kernels for V variations per event.
 int ev_per_tile_for(uint32_t V);

@@ -1,0 +1,73 @@
+"""The allocation-free entry point hf_run_device_noalloc, for callers that
+cannot allocate device memory when they run a chunk (inside a CUDA stream
+capture, in a framework that owns every device allocation, in a real-time
+loop).  The caller allocates the inputs and outputs beforehand; the entry
+point itself allocates nothing and keeps its scratch in one static device
+array.  Its results must equal those of hf_run_device, on two calls in a row
+(the second call sees the first call's leftovers in the shared array).
+
+This file sorts last so that a run stopping at the first failure has already
+run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+from synth import analyses
+from tests.parity import assert_reco
+
+pytestmark = pytest.mark.gpu
+
+
+def _desc(an):
+    from paper_2211_14346_gb300 import _lib, _cut_struct, _f32
+    cuts = _cut_struct(an["cuts"])
+    d = _lib.hf_analysis_desc()
+    d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
+    d.n_cuts = len(an["cuts"])
+    d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
+    for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
+        setattr(d, k, _f32(an[k]))
+    nb, lo, hi = an["hist"]
+    d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
+    return d, cuts
+
+
+def test_noalloc_matches_run_device_twice():
+    import torch
+    from paper_2211_14346_gb300 import build, Engine, DeviceColumns, DeviceResults, _lib, CUDA_STREAM_LEGACY
+    build.build()
+    lib = _lib.load()
+    an = analyses.config2()
+    cols = synth.gen_semilep(20000, 77)
+    dc = DeviceColumns(cols)
+    with Engine(0) as eng:
+        aid = eng.define(an)
+        ref = eng.run_device(aid, dc, V=16, seed=1002, first_event_id=5000).numpy()
+    d, keep = _desc(an)
+    cs = dc.struct()
+    stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+    for call in range(2):
+        out = DeviceResults(cols.n_events, len(an["cuts"]), an["hist"][0])
+        rs = out.struct()
+        st = lib.hf_run_device_noalloc(C.byref(d), C.byref(cs), cols.n_events, 5000, 1002, 16, C.byref(rs),
+                                       C.c_void_p(stream))
+        assert st == _lib.HF_OK, lib.hf_last_error(None)
+        g = out.numpy()
+        assert np.array_equal(g["cutflow"], ref["cutflow"]), (call, g["cutflow"], ref["cutflow"])
+        assert np.array_equal(g["hist"], ref["hist"]), call
+        assert np.array_equal(g["mask"], ref["mask"]), call
+        assert np.array_equal(g["n_surv"], ref["n_surv"]), call
+        assert_reco(g["reco"], ref["reco"], what="noalloc call %d" % call)
+
+
+def test_noalloc_rejects_oversized_chunk():
+    from paper_2211_14346_gb300 import build, _lib
+    build.build()
+    lib = _lib.load()
+    d, keep = _desc(analyses.config2())
+    cs = _lib.hf_columns()
+    st = lib.hf_run_device_noalloc(C.byref(d), C.byref(cs), (1 << 20) + 1, 0, 0, 1, None, None)
+    assert st == _lib.HF_EINVAL
+    assert b"HF_NOALLOC_MAX_EVENTS" in lib.hf_last_error(None)
