@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libhf.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hf_kernels.cu", "hf_s2_semi_a.cu", "hf_s2_semi_b.cu", "hf_s2_semi_c.cu", "hf_plain.cu",
-           "hf_sched.cu", "hf_api.cpp", "hf_noalloc.cu"]
+           "hf_stage2_dilep.cu", "hf_sched.cu", "hf_api.cpp", "hf_noalloc.cu"]
 
 
 def _nvcc():

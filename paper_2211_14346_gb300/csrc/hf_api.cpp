@@ -240,7 +240,6 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     if (!d) return fail(HF_EINVAL, "desc is NULL");
     if (d->event_model != MODEL_SEMILEP && d->event_model != MODEL_DILEP)
         return fail(HF_EINVAL, "unknown event model");
-    if (d->event_model == MODEL_DILEP) return fail(HF_EINVAL, "dilepton model not available in this build");
     if (d->n_cuts < 1 || d->n_cuts > (uint32_t)MAX_CUTS || !d->cuts) return fail(HF_EINVAL, "n_cuts must be 1..16");
     if (!(d->sigma_t > 0) || !(d->sigma_W > 0)) return fail(HF_EINVAL, "widths must be > 0");
     if (!(d->sigma_jet >= 0.0f && d->sigma_jet <= 0.15f))

@@ -6,6 +6,7 @@
 #include "hf_dev.cuh"
 #include "hf_fp64.cuh"
 #include "hf_semilep.cuh"
+#include "hf_dilep_f.cuh"
 
 namespace hf {
 
@@ -282,6 +283,55 @@ static __device__ __noinline__ double hadtop_screened_d(const Plan& P, LazyUnitD
     return best_d;
 }
 
+// Dilepton unit with the definition's FP64 arithmetic (user order).
+static __device__ __noinline__ int dilep_unit_fp64(const Plan& P, const Cols& C, uint32_t e, LazyUnitD& U,
+                                                   unsigned s1bits, float4* reco, int* bin)
+{
+    const float2 mf = C.met[e];
+    double l1[4], l2[4];
+    {
+        float4 a = C.lep[2 * (uint64_t)e], b = C.lep[2 * (uint64_t)e + 1];
+        l1[0] = a.x; l1[1] = a.y; l1[2] = a.z; l1[3] = a.w;
+        l2[0] = b.x; l2[1] = b.y; l2[2] = b.z; l2[3] = b.w;
+    }
+    const unsigned btag = C.btag[e];
+    bool done = false;
+    DilepResD r;
+    auto jet = [&U](int i) { return U.j(i); };
+    int f = P.n_cuts;
+    for (int c = 0; c < P.n_cuts; ++c) {
+        bool pass;
+        if (P.stage1 >> c & 1u) {
+            pass = s1bits >> c & 1u;
+        } else if (P.kind[c] == CUT_MET_MIN) {
+            U.met(mf);
+            pass = sqrt(U.metx * U.metx + U.mety * U.mety) > P.dp0[c];
+        } else {
+            if (!done) {
+                U.met(mf);
+                r = dilep_reco_d(P, U.n, btag, l1, l2, U.metx, U.mety, jet);
+                done = true;
+            }
+            if (P.kind[c] == CUT_DILEP_SOLVABLE) pass = r.ok;
+            else if (P.kind[c] == CUT_HIGGS_WINDOW) pass = r.h_ok && r.m_bb > P.dp0[c] && r.m_bb < P.dp1[c];
+            else pass = false;
+        }
+        if (!pass) {
+            f = c;
+            break;
+        }
+    }
+    if (f == P.n_cuts) {
+        if (!done) {
+            U.met(mf);
+            r = dilep_reco_d(P, U.n, btag, l1, l2, U.metx, U.mety, jet);
+        }
+        *bin = hist_bin_d(P, r.m_bb);
+        *reco = make_float4((float)r.m_bb, (float)r.m_t1, (float)r.m_t2, (float)r.m_tt);
+    }
+    return f;
+}
+
 // One unit with the definition's FP64 decisions (user order; stage-1
 // results are already exact and are taken from s1bits).  Returns the number
 // of leading cuts passed; reco and bin are set when all pass.
@@ -290,6 +340,7 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
 {
     LazyUnitD U;
     U.init(P, C, e, event_id, seed, v);
+    if (P.model == MODEL_DILEP) return dilep_unit_fp64(P, C, e, U, s1bits, reco, bin);
     const float2 mf = C.met[e];
     bool top_done = false;
     double chi2 = 0.0, mtop = 0.0, mw = 0.0;
@@ -403,6 +454,79 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
     }
     atomicAdd(O.rc_total, (unsigned long long)nflag);
     write_event(O, e, cnt, sum, comp);
+}
+
+// ------------------------------------------------------------------ tile epilogues
+// Adds a warp's units to the block's cut flow, histogram and scheduler
+// statistics with one shared-memory atomic per distinct value (lanes with the
+// same first-failure index or bin are combined by __match_any_sync).
+__device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsigned long long* fc, unsigned* hist,
+                                           CutStats* st)
+{
+    const unsigned am = __activemask();
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned g = __match_any_sync(am, r.f);
+    if (r.f >= 0 && lane == (unsigned)(__ffs(g) - 1)) atomicAdd(&fc[r.f], (unsigned long long)__popc(g));
+    const int hb = r.f == P.n_cuts ? r.bin : -1;
+    const unsigned gh = __match_any_sync(am, hb);
+    if (hb >= 0 && lane == (unsigned)(__ffs(gh) - 1)) atomicAdd(&hist[hb], (unsigned)__popc(gh));
+    const bool leader = lane == (unsigned)(__ffs(am) - 1);
+    const unsigned ct = __reduce_add_sync(am, r.cyc_top), cm = __reduce_add_sync(am, r.cyc_met);
+    const unsigned nc = __reduce_add_sync(am, r.cands);
+    if (leader && nc) atomicAdd(&st->cands, (unsigned long long)nc);
+    for (unsigned bits = P.stage2; bits; bits &= bits - 1) {
+        const int c = __ffs(bits) - 1;
+        const unsigned ne = __popc(__ballot_sync(am, r.evald >> c & 1u));
+        const unsigned np = __popc(__ballot_sync(am, r.passd >> c & 1u));
+        if (leader && ne) {
+            atomicAdd(&st->evaluated[c], ne);
+            atomicAdd(&st->passed[c], np);
+            atomicAdd(&st->cost[c], (unsigned long long)(P.kind[c] == CUT_MET_MIN ? cm : ct));
+        }
+    }
+}
+
+// Per-event reduction of a tile's units, one thread per event, in variation
+// order: compensated sums of the surviving units' reconstructed quantities;
+// events without flagged units are written, the others are registered for
+// the FP64 recheck (more than 64 flagged units: the excess is evaluated here).
+__device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+                                          uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
+                                          const uint32_t* bits, const int* uf, const float4* ureco,
+                                          unsigned long long* fc, unsigned* hist)
+{
+    for (int ev = threadIdx.x; ev < ne; ev += blockDim.x) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
+        unsigned cnt = 0;
+        int nflag = 0;
+        uint16_t vs[64];
+        const uint32_t e = evid[ev];
+        for (uint32_t v = 0; v < V; ++v) {
+            const int u = ev * (int)V + (int)v;
+            const int f = uf[u];
+            if (f < 0) {
+                if (nflag < 64) {
+                    vs[nflag++] = (uint16_t)v;
+                } else {
+                    float4 reco;
+                    int bin = 0;
+                    int f2 = unit_fp64(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin);
+                    atomicAdd(&fc[f2], 1ull);
+                    atomicAdd(O.rc_total, 1ull);
+                    if (f2 == P.n_cuts) {
+                        ++cnt;
+                        atomicAdd(&hist[bin], 1u);
+                        acc4(sum, comp, reco);
+                    }
+                }
+            } else if (f == P.n_cuts) {
+                ++cnt;
+                acc4(sum, comp, ureco[u]);
+            }
+        }
+        if (nflag == 0) write_event(O, e, cnt, sum, comp);
+        else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
+    }
 }
 
 // ------------------------------------------------------------------ tile shared memory

@@ -20,7 +20,14 @@
 namespace hf {
 
 // ------------------------------------------------------------------ k_count
-__global__ void k_count(const Cols C, uint32_t N, Scratch S)
+// Bucket of an event: its jet multiplicity (semileptonic: the triplet loop
+// is unrolled per n) or its number of b-tagged jets (dilepton: pairings).
+__device__ __forceinline__ int bucket_key(const Plan& P, const Cols& C, uint32_t e, uint32_t n)
+{
+    return P.model == MODEL_DILEP ? popc_n(C.btag[e], (int)n) : (int)n;
+}
+
+__global__ void k_count(const Plan P, const Cols C, uint32_t N, Scratch S)
 {
     __shared__ unsigned h[16];
     if (threadIdx.x < 16) h[threadIdx.x] = 0;
@@ -28,7 +35,7 @@ __global__ void k_count(const Cols C, uint32_t N, Scratch S)
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
         uint32_t a = C.jet_off[e], b = C.jet_off[e + 1];
         uint32_t n = b - a;
-        if (b >= a && n <= MAX_JETS) atomicAdd(&h[n], 1u);
+        if (b >= a && n <= MAX_JETS) atomicAdd(&h[bucket_key(P, C, e, n)], 1u);
     }
     __syncthreads();
     if (threadIdx.x < NBUCKET && h[threadIdx.x]) atomicAdd(&S.nhist[threadIdx.x], h[threadIdx.x]);
@@ -63,8 +70,8 @@ __global__ void __launch_bounds__(256) k_stage1(const Plan P, const Cols C, uint
             bits = stage1_bits(P, C, e, (int)n);
             int f1 = first_fail_stage1(P, bits);
             if (needs_stage2(P, f1)) {
-                bucket = (int)n;
-                loc = atomicAdd(&s_cnt[n], 1u);
+                bucket = bucket_key(P, C, e, n);
+                loc = atomicAdd(&s_cnt[bucket], 1u);
             } else {
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
                 write_zero_event(O, e);
@@ -153,7 +160,7 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
             cudaEventRecord(ev[2], st);
         }
     } else {
-        k_count<<<min(nb, 4096u), 256, 0, st>>>(C, N, S);
+        k_count<<<min(nb, 4096u), 256, 0, st>>>(P, C, N, S);
         k_stage1<<<nb, 256, 0, st>>>(P, C, N, V, O, S);
         if (ev) cudaEventRecord(ev[1], st);
         const int ept = ev_per_tile_for(V);
@@ -161,9 +168,14 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
             launch_s2_semi<0>, launch_s2_semi<1>, launch_s2_semi<2>,  launch_s2_semi<3>, launch_s2_semi<4>,
             launch_s2_semi<5>, launch_s2_semi<6>, launch_s2_semi<7>,  launch_s2_semi<8>, launch_s2_semi<9>,
             launch_s2_semi<10>, launch_s2_semi<11>, launch_s2_semi<12>};
-        for (int n = NBUCKET - 1; n >= 0; --n) {
-            e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, st);
+        if (P.model == MODEL_DILEP) {
+            e = launch_s2_dilep(P, C, O, S, V, seed, first_id, sms, st);
             if (e != cudaSuccess) return e;
+        } else {
+            for (int n = NBUCKET - 1; n >= 0; --n) {
+                e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, st);
+                if (e != cudaSuccess) return e;
+            }
         }
         if (ev) cudaEventRecord(ev[2], st);
     }

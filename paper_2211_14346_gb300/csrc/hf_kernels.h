@@ -25,6 +25,9 @@ template <int N>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st);
 
+cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
+                            uint64_t first_id, int sms, cudaStream_t st);
+
 cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                          uint64_t seed, uint64_t first_id, cudaStream_t st);
 

@@ -16,35 +16,6 @@
 
 namespace hf {
 
-// Adds a warp's units to the block's cut flow, histogram and scheduler
-// statistics with one shared-memory atomic per distinct value (lanes with the
-// same first-failure index or bin are combined by __match_any_sync).
-__device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsigned long long* fc, unsigned* hist,
-                                           CutStats* st)
-{
-    const unsigned am = __activemask();
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned g = __match_any_sync(am, r.f);
-    if (r.f >= 0 && lane == (unsigned)(__ffs(g) - 1)) atomicAdd(&fc[r.f], (unsigned long long)__popc(g));
-    const int hb = r.f == P.n_cuts ? r.bin : -1;
-    const unsigned gh = __match_any_sync(am, hb);
-    if (hb >= 0 && lane == (unsigned)(__ffs(gh) - 1)) atomicAdd(&hist[hb], (unsigned)__popc(gh));
-    const bool leader = lane == (unsigned)(__ffs(am) - 1);
-    const unsigned ct = __reduce_add_sync(am, r.cyc_top), cm = __reduce_add_sync(am, r.cyc_met);
-    const unsigned nc = __reduce_add_sync(am, r.cands);
-    if (leader && nc) atomicAdd(&st->cands, (unsigned long long)nc);
-    for (unsigned bits = P.stage2; bits; bits &= bits - 1) {
-        const int c = __ffs(bits) - 1;
-        const unsigned ne = __popc(__ballot_sync(am, r.evald >> c & 1u));
-        const unsigned np = __popc(__ballot_sync(am, r.passd >> c & 1u));
-        if (leader && ne) {
-            atomicAdd(&st->evaluated[c], ne);
-            atomicAdd(&st->passed[c], np);
-            atomicAdd(&st->cost[c], (unsigned long long)(P.kind[c] == CUT_HADTOP_CHI2_MAX ? ct : cm));
-        }
-    }
-}
-
 template <int N>
 __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
@@ -98,38 +69,7 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
     }
     __syncthreads();
     // C: per-event reduction in variation order
-    for (int ev = threadIdx.x; ev < ne; ev += blockDim.x) {
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
-        unsigned cnt = 0;
-        int nflag = 0;
-        uint16_t vs[64];
-        const uint32_t e = sm.evid[ev];
-        for (uint32_t v = 0; v < V; ++v) {
-            int u = ev * (int)V + (int)v;
-            int f = sm.uf[u];
-            if (f < 0) {
-                if (nflag < 64) {
-                    vs[nflag++] = (uint16_t)v;
-                } else {  // more than 64 flagged units: evaluate the excess here
-                    float4 reco;
-                    int bin = 0;
-                    int f2 = unit_fp64(P, C, e, first_id + e, seed, v, sm.bits[ev], &reco, &bin);
-                    atomicAdd(&fc[f2], 1ull);
-                    atomicAdd(O.rc_total, 1ull);
-                    if (f2 == P.n_cuts) {
-                        ++cnt;
-                        atomicAdd(&hist[bin], 1u);
-                        acc4(sum, comp, reco);
-                    }
-                }
-            } else if (f == P.n_cuts) {
-                ++cnt;
-                acc4(sum, comp, sm.ureco[u]);
-            }
-        }
-        if (nflag == 0) write_event(O, e, cnt, sum, comp);
-        else pend_event(P, C, O, S, e, first_id + e, seed, sm.bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
-    }
+    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, fc, hist);
     __syncthreads();
 }
 
