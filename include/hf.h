@@ -52,10 +52,16 @@ typedef int32_t hf_status;
 
 typedef struct hf_ctx hf_ctx;
 
+/* Largest number of smearing variations per event of any entry point (the
+ * units of one event share one stage-2 tile in shared memory). */
+#define HF_MAX_VARIATIONS 4096u
+
 /* hf_config.flags */
 #define HF_FLAG_PLAIN 1u      /* run every chunk with the plain one-thread-per-event kernel */
 #define HF_FLAG_NO_SCHED 2u   /* keep the user order for execution (no reordering)         */
 #define HF_FLAG_DEBUG_SYNC 4u /* synchronise after every launch and check errors           */
+#define HF_FLAG_OVERLAP 16u   /* run the per-multiplicity stage-2 kernels of a run on side
+                                 streams so that they overlap (default: one after another)  */
 
 typedef struct {
     int32_t device;            /* CUDA device ordinal                                   */
@@ -115,7 +121,7 @@ typedef struct {
     float mH;            /* Higgs mass for the b-jet pair, GeV (Sect. 4: 125)          */
     float sigma_jet;     /* relative jet-energy resolution of the smearing, [0, 0.15]  */
     float sigma_met;     /* absolute MET resolution per component, GeV, >= 0           */
-    uint32_t hist_nbins; /* reconstructed-mass histogram: bins, 1..4096                */
+    uint32_t hist_nbins; /* reconstructed-mass histogram: bins, 1..1024                */
     float hist_lo, hist_hi; /* range, GeV; hist_lo < hist_hi                            */
 } hf_analysis_desc;
 
@@ -153,7 +159,7 @@ typedef struct {
  * that must stay valid and unchanged until the ticket is DONE or FAILED
  * (the library copies them to the device, from pinned memory directly or via
  * its pinned staging).  first_event_id is the global id of event 0 (it keys
- * the smearing); seed keys the smearing; n_variations = V >= 1.
+ * the smearing); seed keys the smearing; n_variations = V in 1..HF_MAX_VARIATIONS.
  * *ticket receives the ticket.  Errors: HF_EINVAL (bad columns or sizes),
  * HF_ENOTFOUND (analysis), HF_EBUSY (budget or slots; nothing enqueued),
  * HF_ENOMEM, HF_ECUDA.  Malformed offsets or n_jets > 12 found on the device
@@ -195,8 +201,43 @@ hf_status hf_run_device_plain(hf_ctx* ctx, uint32_t analysis_id, const hf_column
                               uint64_t n_events, uint64_t first_event_id, uint64_t seed,
                               uint32_t n_variations, const hf_results* dev_out, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Batched runs: many chunks through one fixed launch sequence.         */
+/* ------------------------------------------------------------------ */
+/* One chunk of a batch: its analysis, smearing keys, DEVICE columns and
+ * DEVICE result buffers (caller-owned; NULL result fields are skipped, the
+ * cut flow and histogram are overwritten, not accumulated). */
+typedef struct {
+    uint32_t analysis_id;    /* registered analysis, either event model               */
+    uint32_t n_variations;   /* V in 1..HF_MAX_VARIATIONS                              */
+    uint64_t n_events;       /* N < 2^32 (0 allowed)                                   */
+    uint64_t first_event_id; /* global id of event 0 (keys the smearing)               */
+    uint64_t seed;           /* smearing seed                                          */
+    hf_columns cols;         /* DEVICE columns, layout as for hf_run_device            */
+    hf_results out;          /* DEVICE results of this chunk                           */
+} hf_chunk;
+
+/* Runs n_chunks chunks of uneven size -- any mix of analyses (hence of the
+ * semileptonic and dilepton models), sizes and variation counts -- on
+ * `stream` (NULL = the context's stream) through one fixed sequence of
+ * persistent kernels: a column scan and compaction over all chunks, one
+ * stage-2 grid per jet multiplicity (and one for the dilepton model) that
+ * takes tiles of every chunk from a device work queue, and one FP64 recheck
+ * (Sect. 3: every chunk's events pass the ordered cut chain; Sect. 5: many
+ * independent event sets processed concurrently).  The sequence does not
+ * depend on the number of chunks; the context captures it once as a CUDA
+ * graph and replays the graph for later batches that fit the same scratch
+ * layout.  Each chunk's results equal those of hf_run_device on that chunk.
+ * Cut execution orders are each analysis's current ones; the scheduler
+ * updates each analysis once after the batch from the batch's statistics.
+ * chunks: HOST array (copied by the call).  The context's scratch arena is
+ * grown as needed (device allocation outside any stream capture).
+ * Errors: HF_EINVAL (a chunk's sizes, pointers or V), HF_ENOTFOUND (analysis),
+ * HF_ENOMEM, HF_ECUDA.  Malformed columns set the device error word. */
+hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, void* stream);
+
 /* Waits for the context's stream and returns the device error word of the
- * last hf_run_device* call in *word (0 = none; bit 0 = malformed offsets or
+ * last hf_run_device* or hf_run_batch call in *word (0 = none; bit 0 = malformed offsets or
  * n_jets > 12).  Errors: HF_ECUDA. */
 hf_status hf_device_error(hf_ctx* ctx, uint32_t* word);
 

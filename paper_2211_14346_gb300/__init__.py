@@ -15,7 +15,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HF_FLAG_PROFILE, HFError,  # noqa: F401
+from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HF_FLAG_PROFILE, HF_FLAG_OVERLAP,  # noqa: F401
+                   HFError,
                    HF_STATE_DONE, HF_STATE_FAILED, HF_STATE_QUEUED, HF_STATE_RUNNING)
 
 N_RECO = 4
@@ -200,6 +201,33 @@ class Engine:
         self._check(fn(self.ctx, aid, C.byref(cs), dcols.n_events, first_event_id, seed, V, C.byref(rs),
                        stream))
         return out
+
+    def run_batch(self, items, *, stream=None):
+        """Runs many chunks through one batched launch sequence.
+
+        items: iterable of dicts with keys aid, cols (DeviceColumns), V, seed,
+        first_event_id, out (DeviceResults, created when absent).  Returns the
+        list of DeviceResults in the order of items."""
+        items = list(items)
+        arr = (_lib.hf_chunk * max(1, len(items)))()
+        outs = []
+        for k, it in enumerate(items):
+            dc = it["cols"]
+            out = it.get("out") or self.results_for(it["aid"], dc.n_events)
+            outs.append(out)
+            c = arr[k]
+            c.analysis_id = it["aid"]
+            c.n_variations = it.get("V", 1)
+            c.n_events = dc.n_events
+            c.first_event_id = it.get("first_event_id", 0)
+            c.seed = it.get("seed", 0)
+            c.cols = dc.struct()
+            c.out = out.struct(it.get("fields"))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+        self._check(self.lib.hf_run_batch(self.ctx, arr, len(items), stream))
+        return outs
 
     def device_error(self):
         w = C.c_uint32()

@@ -25,6 +25,7 @@ HF_FLAG_PLAIN = 1
 HF_FLAG_NO_SCHED = 2
 HF_FLAG_DEBUG_SYNC = 4
 HF_FLAG_PROFILE = 8
+HF_FLAG_OVERLAP = 16
 
 HF_MODEL_SEMILEP = 1
 HF_MODEL_DILEP = 2
@@ -60,6 +61,11 @@ class hf_columns(C.Structure):
 class hf_results(C.Structure):
     _fields_ = [("mask", C.c_void_p), ("cutflow", C.c_void_p), ("hist", C.c_void_p), ("n_surv", C.c_void_p),
                 ("reco", C.c_void_p), ("recheck_count", C.c_void_p)]
+
+
+class hf_chunk(C.Structure):
+    _fields_ = [("analysis_id", C.c_uint32), ("n_variations", C.c_uint32), ("n_events", C.c_uint64),
+                ("first_event_id", C.c_uint64), ("seed", C.c_uint64), ("cols", hf_columns), ("out", hf_results)]
 
 
 class hf_profile_data(C.Structure):
@@ -99,6 +105,7 @@ def load():
         "hf_profile": ([vp, C.POINTER(hf_profile_data), i32], i32),
         "hf_run_device_noalloc": ([C.POINTER(hf_analysis_desc), C.POINTER(hf_columns), u64, u64, u64, u32,
                                    C.POINTER(hf_results), vp], i32),
+        "hf_run_batch": ([vp, C.POINTER(hf_chunk), u32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -112,7 +119,7 @@ def declared_symbols():
     """Names of the entry points this binding marshals (the ones hf.h declares)."""
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
-            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc"]
+            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch"]
 
 
 class HFError(RuntimeError):

@@ -16,6 +16,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -139,6 +140,7 @@ Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
     S.prof = nullptr;
     S.exec2 = A.sched ? A.sched->exec2 : nullptr;
     S.n_exec2 = A.plan.n_exec2;
+    S.chunk = 0;
     return S;
 }
 
@@ -205,6 +207,7 @@ struct hf_ctx {
     uint32_t max_inflight = 64;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     cudaStream_t user_stream = nullptr;
+    SideStreams side{};  // stage-2 kernels of one run overlap on these
     std::mutex mu;
     std::vector<std::unique_ptr<Analysis>> analyses;
     // scratch arena for device-resident runs
@@ -215,6 +218,14 @@ struct hf_ctx {
     std::map<uint64_t, Ticket> tickets;
     uint64_t next_ticket = 1;
     uint64_t inflight_bytes = 0;
+    // batched runs: pinned staging of the batch tables, the captured launch
+    // sequence and what it was captured for
+    char* bstage = nullptr;
+    size_t bstage_bytes = 0;
+    cudaEvent_t bstage_free = nullptr;  // last upload from the staging buffer
+    cudaStream_t s_cap = nullptr;       // capture stream of the batch graph
+    cudaGraphExec_t bgraph = nullptr;
+    std::vector<uint64_t> bgraph_key;
     // profiling (HF_FLAG_PROFILE)
     unsigned long long* prof_dev = nullptr;  // u64[64] device counters
     std::vector<std::array<cudaEvent_t, 4>> prof_events;  // phases of runs not yet summed
@@ -347,6 +358,11 @@ hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
         ctx->arena = nullptr;
         ctx->arena_bytes = 0;
     }
+    if (ctx->bgraph) {  // captured for the old arena
+        cudaGraphExecDestroy(ctx->bgraph);
+        ctx->bgraph = nullptr;
+        ctx->bgraph_key.clear();
+    }
     size_t want = std::max(bytes, (size_t)64 << 20);
     cudaError_t e = cudaMalloc((void**)&ctx->arena, want);
     if (e != cudaSuccess) {
@@ -383,7 +399,7 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
         for (auto& x : ev) HF_CUDA(cudaEventCreate(&x));
         evp = ev.data();
     }
-    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st, evp));
+    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st, evp, &ctx->side));
     if (evp) ctx->prof_events.push_back(ev);
     if (!use_plain && A.sched) HF_CUDA(launch_sched_update(A.sched, S.stats, st));
     if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
@@ -418,7 +434,7 @@ hf_status run_device_impl(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* d
     if (hf_status s = use_device(ctx)) return s;
     Analysis* A = get_analysis(ctx, analysis_id);
     if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
-    if (V < 1 || V > 65535) return fail(HF_EINVAL, "n_variations must be 1..65535");
+    if (V < 1 || V > HF_MAX_VARIATIONS) return fail(HF_EINVAL, "n_variations must be 1..4096");
     int L = A->plan.model == MODEL_DILEP ? 2 : 1;
     if (hf_status s = check_cols(dev_cols, N, L)) return s;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
@@ -477,6 +493,12 @@ hf_status hf_open(const hf_config* cfg, hf_ctx** out)
     HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking));
     HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking));
     HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking));
+    ctx->side.n = (ctx->flags & HF_FLAG_OVERLAP) ? MAX_SIDE : 0;
+    for (int i = 0; i < ctx->side.n; ++i) {
+        HF_CUDA(cudaStreamCreateWithFlags(&ctx->side.s[i], cudaStreamNonBlocking));
+        HF_CUDA(cudaEventCreateWithFlags(&ctx->side.join[i], cudaEventDisableTiming));
+    }
+    HF_CUDA(cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming));
     ctx->user_stream = (cudaStream_t)cfg->stream;
     if (ctx->flags & HF_FLAG_PROFILE) {
         HF_CUDA(cudaMalloc((void**)&ctx->prof_dev, 64 * sizeof(unsigned long long)));
@@ -507,7 +529,8 @@ hf_status hf_close(hf_ctx* ctx)
         cudaSetDevice(ctx->device);
         // bounded wait for all streams
         auto t0 = std::chrono::steady_clock::now();
-        cudaStream_t ss[3] = {ctx->s_h2d, ctx->s_comp, ctx->s_d2h};
+        std::vector<cudaStream_t> ss = {ctx->s_h2d, ctx->s_comp, ctx->s_d2h};
+        for (int i = 0; i < ctx->side.n; ++i) ss.push_back(ctx->side.s[i]);
         for (cudaStream_t s : ss) {
             while (cudaStreamQuery(s) == cudaErrorNotReady) {
                 if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
@@ -521,6 +544,10 @@ hf_status hf_close(hf_ctx* ctx)
         }
         for (auto& a : ctx->analyses)
             if (a->sched) cudaFree(a->sched);
+        if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+        if (ctx->bstage) cudaFreeHost(ctx->bstage);
+        if (ctx->bstage_free) cudaEventDestroy(ctx->bstage_free);
+        if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->arena_free) cudaEventDestroy(ctx->arena_free);
         if (ctx->prof_dev) cudaFree(ctx->prof_dev);
@@ -529,6 +556,11 @@ hf_status hf_close(hf_ctx* ctx)
         cudaStreamDestroy(ctx->s_h2d);
         cudaStreamDestroy(ctx->s_comp);
         cudaStreamDestroy(ctx->s_d2h);
+        for (int i = 0; i < ctx->side.n; ++i) {
+            cudaStreamDestroy(ctx->side.s[i]);
+            cudaEventDestroy(ctx->side.join[i]);
+        }
+        if (ctx->side.fork) cudaEventDestroy(ctx->side.fork);
     }
     delete ctx;
     return HF_OK;
@@ -606,7 +638,7 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
     if (hf_status s = use_device(ctx)) return s;
     Analysis* A = get_analysis(ctx, analysis_id);
     if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
-    if (V < 1 || V > 65535) return fail(HF_EINVAL, "n_variations must be 1..65535");
+    if (V < 1 || V > HF_MAX_VARIATIONS) return fail(HF_EINVAL, "n_variations must be 1..4096");
     const int L = A->plan.model == MODEL_DILEP ? 2 : 1;
     if (hf_status s = check_cols(hc, N, L)) return s;
     if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per chunk");
@@ -850,3 +882,267 @@ hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched runs
+namespace {
+
+struct BatchLayout {
+    size_t off_dev, off_ch, off_plans, off_exec, off_stats, off_tpre, off_cnt, off_tctr, off_fb, off_bucket, off_rc,
+        off_pend_cnt, off_pend_left, off_pend_sum, off_pend_comp, bytes;
+    size_t table_bytes;  // [off_dev, off_fb): uploaded from the host
+    unsigned rc_cap;
+};
+
+}  // namespace
+
+extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, void* stream)
+{
+    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    if (n_chunks > 0 && !chunks) return fail(HF_EINVAL, "chunks is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
+    if (n_chunks == 0) return HF_OK;
+    // validate; semileptonic chunks first (the kernels take each model's chunks as one range)
+    std::vector<uint32_t> order;
+    order.reserve(n_chunks);
+    for (int pass = 0; pass < 2; ++pass)
+        for (uint32_t i = 0; i < n_chunks; ++i) {
+            const hf_chunk& k = chunks[i];
+            Analysis* A = get_analysis(ctx, k.analysis_id);
+            if (!A) return fail(HF_ENOTFOUND, "a chunk names an unknown analysis id");
+            if ((A->plan.model == MODEL_DILEP) != (pass == 1)) continue;
+            if (k.n_variations < 1 || k.n_variations > HF_MAX_VARIATIONS)
+                return fail(HF_EINVAL, "a chunk's n_variations is outside 1..4096");
+            if (k.n_events > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per chunk");
+            if (hf_status s = check_cols(&k.cols, k.n_events, 1)) return s;
+            if (k.out.reco && ((uintptr_t)k.out.reco & 15)) return fail(HF_EINVAL, "reco must be 16-byte aligned");
+            order.push_back(i);
+        }
+    // plans of the batch
+    std::vector<uint32_t> plan_ids;  // analysis id per plan index
+    std::map<uint32_t, uint32_t> plan_of;
+    for (uint32_t i : order) {
+        uint32_t a = chunks[i].analysis_id;
+        if (!plan_of.count(a)) {
+            plan_of[a] = (uint32_t)plan_ids.size();
+            plan_ids.push_back(a);
+        }
+    }
+    const uint32_t nc = n_chunks, np = (uint32_t)plan_ids.size();
+    // host tables
+    std::vector<BChunk> tab(nc);
+    uint64_t ev_total = 0, blocks = 0, units_semi = 0, units_dl = 0, fb_words = 0;
+    uint32_t n_semi = 0;
+    BatchLaunch BL;
+    memset(&BL, 0, sizeof BL);
+    BL.sms = ctx->sms;
+    for (uint32_t x = 0; x < nc; ++x) {
+        const hf_chunk& k = chunks[order[x]];
+        Analysis* A = get_analysis(ctx, k.analysis_id);
+        const Plan& P = A->plan;
+        BChunk& b = tab[x];
+        memset(&b, 0, sizeof b);
+        b.C.jet_off = k.cols.jet_off;
+        b.C.jets = (const float4*)k.cols.jets;
+        b.C.btag = k.cols.btag;
+        b.C.lep = (const float4*)k.cols.lep;
+        b.C.lep_q = k.cols.lep_q;
+        b.C.met = (const float2*)k.cols.met;
+        b.C.n_jets_total = k.cols.n_jets_total;
+        b.O.mask = k.out.mask;
+        b.O.n_surv = k.out.n_surv;
+        b.O.reco = (float4*)k.out.reco;
+        b.O.cutflow = (unsigned long long*)k.out.cutflow;
+        b.O.hist = (unsigned long long*)k.out.hist;
+        b.O.rc_total = (unsigned long long*)k.out.recheck_count;
+        if (!b.O.cutflow) fb_words += MAX_CUTS + 1;
+        if (!b.O.hist) fb_words += MAX_BINS + 2;
+        if (!b.O.rc_total) fb_words += 1;
+        b.seed = k.seed;
+        b.first_id = k.first_event_id;
+        b.V = k.n_variations;
+        b.n = (uint32_t)k.n_events;
+        b.plan = plan_of[k.analysis_id];
+        b.model = (uint32_t)P.model;
+        b.blk0 = (uint32_t)blocks;
+        b.ev0 = ev_total;
+        const uint64_t units = (uint64_t)b.n * b.V;
+        if (P.model == MODEL_DILEP) {
+            b.ept = (uint32_t)dl_ev_per_tile(b.V);
+            BL.dilep = true;
+            BL.smem_dilep = std::max(BL.smem_dilep, dl_smem_bytes((int)b.ept, (int)(b.ept * b.V)));
+            units_dl += units;
+        } else {
+            b.ept = (uint32_t)ev_per_tile_for(b.V);
+            ++n_semi;
+            BL.semi_mask = (1u << NBUCKET) - 1;
+            for (int n = 0; n < NBUCKET; ++n)
+                BL.smem_semi[n] = std::max(BL.smem_semi[n], semi_tile_bytes(n, (int)b.ept, (int)(b.ept * b.V)));
+            units_semi += units;
+        }
+        ev_total += b.n;
+        blocks += (b.n + BLOCK1 - 1) / BLOCK1;
+    }
+    if (blocks >= (1ull << 31)) return fail(HF_EINVAL, "batch too large (stage-1 blocks)");
+    // device layout (one region of the context's arena)
+    BatchLayout L;
+    size_t o = 0;
+    L.off_dev = o;
+    o += sizeof(BatchDev);
+    L.off_ch = o = align_up(o, 256);
+    o += sizeof(BChunk) * nc;
+    L.off_plans = o = align_up(o, 256);
+    o += sizeof(Plan) * np;
+    L.off_exec = o = align_up(o, 256);
+    o += sizeof(void*) * np;
+    L.table_bytes = o;
+    L.off_stats = o = align_up(o, 256);
+    o += 8 * 3 * MAX_CUTS * (size_t)np;
+    L.off_tpre = o = align_up(o, 256);
+    o += 4 * (size_t)NBUCKET * (nc + 1);
+    L.off_cnt = o = align_up(o, 256);
+    o += 4 * 32 * (size_t)nc;
+    L.off_tctr = o = align_up(o, 256);
+    o += 4 * 16;
+    L.off_fb = o = align_up(o, 256);
+    o += 8 * fb_words;
+    L.off_bucket = o = align_up(o, 256);
+    o += sizeof(uint2) * std::max<uint64_t>(ev_total, 1);
+    // recheck capacity: ~0.05 % of semileptonic and ~5 % of dilepton units are
+    // flagged; beyond the list the units are evaluated in place (slower, exact)
+    uint64_t cap = 65536 + units_semi / 256 + units_dl / 16;
+    cap = std::min<uint64_t>(cap, 1u << 28);
+    L.rc_cap = (unsigned)cap;
+    L.off_rc = o = align_up(o, 256);
+    o += sizeof(RcEntry) * cap;
+    L.off_pend_cnt = o = align_up(o, 256);
+    o += 4 * cap;
+    L.off_pend_left = o = align_up(o, 256);
+    o += 4 * cap;
+    L.off_pend_sum = o = align_up(o, 256);
+    o += 16 * cap;
+    L.off_pend_comp = o = align_up(o, 256);
+    o += 16 * cap;
+    L.bytes = align_up(o, 256);
+    // the small counter block of single runs (error word at SM_ERR) stays at the
+    // arena's start, so that hf_device_error reads batches too
+    const size_t base_off = 256;
+    if (hf_status s = ensure_arena(ctx, base_off + L.bytes)) return s;
+    if (ctx->arena_free) HF_CUDA(cudaStreamWaitEvent(st, ctx->arena_free, 0));
+    char* dbase = ctx->arena + base_off;
+    // fill in device addresses
+    unsigned* cnt = (unsigned*)(dbase + L.off_cnt);
+    unsigned long long* fb = (unsigned long long*)(dbase + L.off_fb);
+    for (uint32_t x = 0; x < nc; ++x) {
+        BChunk& b = tab[x];
+        b.cnt = cnt + 32 * (size_t)x;
+        if (!b.O.cutflow) { b.O.cutflow = fb; fb += MAX_CUTS + 1; }
+        if (!b.O.hist) { b.O.hist = fb; fb += MAX_BINS + 2; }
+        if (!b.O.rc_total) { b.O.rc_total = fb; fb += 1; }
+    }
+    BatchDev B;
+    memset(&B, 0, sizeof B);
+    B.ch = (const BChunk*)(dbase + L.off_ch);
+    B.plans = (const Plan*)(dbase + L.off_plans);
+    B.exec = (const int* const*)(dbase + L.off_exec);
+    B.stats = (unsigned long long*)(dbase + L.off_stats);
+    B.tpre = (unsigned*)(dbase + L.off_tpre);
+    B.tctr = (unsigned*)(dbase + L.off_tctr);
+    B.bucket = (uint2*)(dbase + L.off_bucket);
+    B.n_chunks = nc;
+    B.n_semi = n_semi;
+    B.n_blocks = (uint32_t)blocks;
+    B.n_plans = np;
+    {
+        Scratch& S = B.S;
+        char* sm = ctx->arena;  // small counter block of the arena
+        S.nhist = S.cursor = S.tile_ctr = nullptr;
+        S.rc_count = (unsigned*)(sm + SM_RC);
+        S.rc_valid = (unsigned*)(sm + SM_RCVALID);
+        S.pend_count = (unsigned*)(sm + SM_PEND);
+        S.err = (unsigned*)(sm + SM_ERR);
+        S.bucket = B.bucket;
+        S.rc = (RcEntry*)(dbase + L.off_rc);
+        S.rc_cap = L.rc_cap;
+        S.pend_cnt = (unsigned*)(dbase + L.off_pend_cnt);
+        S.pend_left = (unsigned*)(dbase + L.off_pend_left);
+        S.pend_sum = (float4*)(dbase + L.off_pend_sum);
+        S.pend_comp = (float4*)(dbase + L.off_pend_comp);
+        S.stats = nullptr;
+        S.prof = nullptr;
+        S.exec2 = nullptr;
+        S.n_exec2 = 0;
+        S.chunk = 0;
+    }
+    // host staging of the tables (pinned; reused once its last upload is done)
+    if (ctx->bstage_free) HF_CUDA(cudaEventSynchronize(ctx->bstage_free));
+    if (ctx->bstage_bytes < L.table_bytes) {
+        if (ctx->bstage) cudaFreeHost(ctx->bstage);
+        ctx->bstage = nullptr;
+        ctx->bstage_bytes = 0;
+        size_t want = std::max(L.table_bytes, (size_t)1 << 20);
+        if (cudaHostAlloc((void**)&ctx->bstage, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HF_ENOMEM, "pinned staging of the batch tables failed");
+        }
+        ctx->bstage_bytes = want;
+    }
+    char* h = ctx->bstage;
+    memcpy(h + L.off_dev, &B, sizeof B);
+    memcpy(h + L.off_ch, tab.data(), sizeof(BChunk) * nc);
+    for (uint32_t p = 0; p < np; ++p) {
+        Analysis* A = get_analysis(ctx, plan_ids[p]);
+        memcpy(h + L.off_plans + sizeof(Plan) * p, &A->plan, sizeof(Plan));
+        if (!A->sched) return fail(HF_ESTATE, "analysis without scheduler state");
+        // device address of the execution order inside the analysis's SchedDev
+        const int* ex = (const int*)((const char*)A->sched + offsetof(SchedDev, exec2));
+        memcpy(h + L.off_exec + sizeof(void*) * p, &ex, sizeof(void*));
+    }
+    HF_CUDA(cudaMemcpyAsync(dbase, h, L.table_bytes, cudaMemcpyHostToDevice, st));
+    if (!ctx->bstage_free) HF_CUDA(cudaEventCreateWithFlags(&ctx->bstage_free, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(ctx->bstage_free, st));
+    // the launch sequence: replay the captured graph when it was captured for
+    // the same arena, table layout, launch shape and scheduler states
+    const BatchDev* Bd = (const BatchDev*)(dbase + L.off_dev);
+    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)Bd, (uint64_t)ctx->side.n, BL.semi_mask, BL.dilep,
+                                 BL.smem_dilep, np};
+    for (int n = 0; n < NBUCKET; ++n) key.push_back(BL.smem_semi[n]);
+    for (uint32_t p = 0; p < np; ++p) {
+        Analysis* A = get_analysis(ctx, plan_ids[p]);
+        key.push_back((uint64_t)(uintptr_t)A->sched);
+        key.push_back(A->no_sched ? 1 : 0);
+    }
+    if (!(ctx->bgraph && ctx->bgraph_key == key)) {
+        if (ctx->bgraph) {
+            cudaGraphExecDestroy(ctx->bgraph);
+            ctx->bgraph = nullptr;
+            ctx->bgraph_key.clear();
+        }
+        if (!ctx->s_cap) HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking));
+        HF_CUDA(cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_batch(Bd, BL, ctx->s_cap, &ctx->side);
+        for (uint32_t p = 0; p < np && e == cudaSuccess; ++p) {
+            Analysis* A = get_analysis(ctx, plan_ids[p]);
+            e = launch_sched_update(A->sched, B.stats + (size_t)p * 3 * MAX_CUTS, ctx->s_cap);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e != cudaSuccess ? e : e2, "capturing the batch launch sequence");
+        }
+        e = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->bgraph = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate(batch)");
+        }
+        ctx->bgraph_key = key;
+    }
+    HF_CUDA(cudaGraphLaunch(ctx->bgraph, st));
+    if (!ctx->arena_free) HF_CUDA(cudaEventCreateWithFlags(&ctx->arena_free, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(ctx->arena_free, st));
+    if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
+    return HF_OK;
+}

@@ -432,9 +432,9 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
         for (int i = 0; i < nflag; ++i) {
             RcEntry r;
             r.event = e;
-            r.v = vs[i];
-            r.s1bits = s1bits;
+            r.vbits = (uint32_t)vs[i] | (s1bits << 16);
             r.slot = slot;
+            r.chunk = S.chunk;
             S.rc[base + i] = r;
         }
         return;
@@ -530,9 +530,11 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
 }
 
 // ------------------------------------------------------------------ tile shared memory
+// Shared memory of one semileptonic stage-2 tile: per event the packed Gram
+// matrix (gst floats), lepton, MET, index and stage-1 bits; per unit its
+// result.  The layout depends on the tile's (events, units, stride) only.
 struct TileSmem {
-    float4* jets;   // [ev][12]
-    float* G;       // [ev][GS]: full symmetric Gram matrix, row stride n
+    float* G;       // [ev][gst]
     float4* lep;    // [ev]
     float2* met;    // [ev]
     uint32_t* evid; // [ev]
@@ -540,21 +542,19 @@ struct TileSmem {
     float4* ureco;  // [unit]
     int* uf;        // [unit] f or -1
 };
-constexpr int GS = 145;  // event stride of the Gram matrices: 12 x 12 + 1
 
-__host__ __device__ inline size_t tile_smem_bytes(int ev, int units)
+__host__ __device__ inline size_t tile_smem_bytes(int ev, int units, int gst)
 {
-    return (size_t)ev * (12 * 16 + GS * 4 + 16 + 8 + 4 + 4) + (size_t)units * (16 + 4) + 64;
+    return (size_t)ev * ((size_t)gst * 4 + 16 + 8 + 4 + 4) + (size_t)units * (16 + 4) + 64;
 }
 
-__device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap)
+__device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap, int gst)
 {
     TileSmem t;
-    t.jets = (float4*)p; p += (size_t)ev_cap * 12 * 16;
     t.ureco = (float4*)p; p += (size_t)unit_cap * 16;
     t.lep = (float4*)p; p += (size_t)ev_cap * 16;
     t.met = (float2*)p; p += (size_t)ev_cap * 8;
-    t.G = (float*)p; p += (size_t)ev_cap * GS * 4;
+    t.G = (float*)p; p += (size_t)ev_cap * gst * 4;
     t.evid = (uint32_t*)p; p += (size_t)ev_cap * 4;
     t.bits = (uint32_t*)p; p += (size_t)ev_cap * 4;
     t.uf = (int*)p;

@@ -90,9 +90,9 @@ struct Out {
 // band of a decision (cut threshold, argmin near-tie, histogram edge, ...).
 struct RcEntry {
     uint32_t event;   // index within the chunk
-    uint32_t v;       // variation
-    uint32_t s1bits;  // stage-1 pass bits of the event
+    uint32_t vbits;   // variation (low 16 bits) | stage-1 pass bits of the event << 16
     uint32_t slot;    // pending-event slot
+    uint32_t chunk;   // chunk of a batched run (0 for a single chunk)
 };
 
 struct Scratch {
@@ -114,6 +114,42 @@ struct Scratch {
     unsigned long long* prof;   // [64] profiling counters (PROF_*) or null
     const int* exec2;     // [MAX_CUTS] device execution order of stage-2 cuts (or null)
     int n_exec2;
+    uint32_t chunk;       // chunk index recorded in recheck entries (batched runs)
+};
+
+// ------------------------------------------------------------------ batched runs
+// One chunk of a batched run (device memory; the table is sorted so that
+// semileptonic chunks come first).  Its cut flow, histogram and recheck
+// counter pointers are never null (the batch's scratch provides them).
+struct BChunk {
+    Cols C;
+    Out O;
+    uint64_t seed, first_id;
+    uint32_t V;        // variations per event
+    uint32_t n;        // events
+    uint32_t plan;     // index into BatchDev::plans
+    uint32_t ept;      // events per stage-2 tile
+    uint32_t blk0;     // first stage-1 block of the chunk (BLOCK1 events per block)
+    uint32_t model;
+    uint64_t ev0;      // first bucket slot of the chunk in the batch's bucket array
+    unsigned* cnt;     // [32] nhist[16] | cursor[16] of the chunk
+};
+
+constexpr int BLOCK1 = 256;  // events per stage-1 block
+
+// Everything the kernels of a batched run share (passed by value).
+struct BatchDev {
+    const BChunk* ch;             // n_chunks entries
+    const Plan* plans;            // per analysis of the batch
+    const int* const* exec;       // [plans] stage-2 execution order of each plan (its scheduler's)
+    unsigned long long* stats;    // [plans][3*MAX_CUTS] scheduler statistics of the batch
+    unsigned* tpre;               // [NBUCKET][n_chunks+1] tile prefix over chunks per bucket
+    unsigned* tctr;               // [16] tile counters: semileptonic per multiplicity, [15] dilepton
+    uint2* bucket;                // stage-2 work of every chunk (chunk c from ev0)
+    uint32_t n_chunks, n_semi;    // chunks [0, n_semi) are semileptonic
+    uint32_t n_blocks;            // stage-1 blocks of the batch
+    uint32_t n_plans;
+    Scratch S;                    // recheck list, pending slots, error word of the batch
 };
 
 // ------------------------------------------------------------------ Philox

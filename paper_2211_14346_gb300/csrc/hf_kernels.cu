@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
         RcEntry r = S.rc[i];
         float4 reco;
         int bin = 0;
-        int f = unit_fp64(P, C, r.event, first_id + r.event, seed, r.v, r.s1bits, &reco, &bin);
+        int f = unit_fp64(P, C, r.event, first_id + r.event, seed, r.vbits & 0xffffu, r.vbits >> 16, &reco, &bin);
         ++mine;
         atomicAdd(&s_fc[f], 1ull);
         if (f == P.n_cuts) {
@@ -134,6 +134,8 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
 }
 
 // ------------------------------------------------------------------ host launchers
+size_t semi_tile_bytes(int n, int ept, int units) { return tile_smem_bytes(ept, units, gram_stride(n)); }
+
 int ev_per_tile_for(uint32_t V)
 {
     int e = UNITS_PER_TILE / (int)V;
@@ -146,7 +148,8 @@ typedef cudaError_t (*S2Launcher)(const Plan&, const Cols&, const Out&, const Sc
                                   uint64_t, int, int, cudaStream_t);
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
-                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st, cudaEvent_t* ev)
+                       uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st, cudaEvent_t* ev,
+                       const SideStreams* side)
 {
     if (N == 0) return cudaSuccess;
     const unsigned nb = (N + 255) / 256;
@@ -172,9 +175,24 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
             e = launch_s2_dilep(P, C, O, S, V, seed, first_id, sms, st);
             if (e != cudaSuccess) return e;
         } else {
-            for (int n = NBUCKET - 1; n >= 0; --n) {
-                e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, st);
+            // Buckets are independent: on side streams their persistent grids
+            // overlap, so that the tail of one multiplicity is filled by the next.
+            const bool fork = side && side->n > 0;
+            if (fork) {
+                if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
+                for (int i = 0; i < side->n; ++i)
+                    if ((e = cudaStreamWaitEvent(side->s[i], side->fork, 0)) != cudaSuccess) return e;
+            }
+            for (int n = NBUCKET - 1, x = 0; n >= 0; --n, ++x) {
+                cudaStream_t sn = fork ? side->s[x % side->n] : st;
+                e = semi[n](P, C, O, S, V, seed, first_id, ept, sms, sn);
                 if (e != cudaSuccess) return e;
+            }
+            if (fork) {
+                for (int i = 0; i < side->n; ++i) {
+                    if ((e = cudaEventRecord(side->join[i], side->s[i])) != cudaSuccess) return e;
+                    if ((e = cudaStreamWaitEvent(st, side->join[i], 0)) != cudaSuccess) return e;
+                }
             }
         }
         if (ev) cudaEventRecord(ev[2], st);

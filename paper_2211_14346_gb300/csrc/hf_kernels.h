@@ -30,10 +30,42 @@ cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Sc
 
 cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                          uint64_t seed, uint64_t first_id, cudaStream_t st);
+cudaError_t launch_plain_dilep(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
+                               uint64_t seed, uint64_t first_id, cudaStream_t st);
+
+// Side streams on which the per-multiplicity stage-2 kernels of one run
+// overlap (fork after stage 1, join before the recheck).  Owned by the caller.
+constexpr int MAX_SIDE = 4;
+struct SideStreams {
+    int n;                     // 0 = everything on the run's stream
+    cudaStream_t s[MAX_SIDE];
+    cudaEvent_t fork;          // recorded on the run's stream after stage 1
+    cudaEvent_t join[MAX_SIDE];
+};
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                        uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st,
-                       cudaEvent_t* ev = nullptr);
+                       cudaEvent_t* ev = nullptr, const SideStreams* side = nullptr);
+
+// Batched runs (hf_batch.cu): the host-side shape of one batch's launches.
+struct BatchLaunch {
+    int sms;
+    unsigned semi_mask;            // bit n: some semileptonic chunk has events with n jets
+    size_t smem_semi[NBUCKET];     // dynamic shared memory of the multiplicity-n kernel
+    bool dilep;                    // the batch has dilepton chunks
+    size_t smem_dilep;
+};
+typedef cudaError_t (*BS2Launcher)(const BatchDev*, size_t, int, cudaStream_t);
+template <int N>
+cudaError_t launch_bs2_semi(const BatchDev* B, size_t smem, int sms, cudaStream_t st);
+cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream_t st);
+// Enqueues the whole batch (B in device memory) on st; stage-2 kernels overlap
+// on the side streams when given.
+cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t st, const SideStreams* side);
+// Shared memory of one stage-2 tile (semileptonic multiplicity n / dilepton).
+size_t semi_tile_bytes(int n, int ept, int units);
+size_t dl_smem_bytes(int ev, int units);
+int dl_ev_per_tile(uint32_t V);
 
 // Kernel launches of one fast-path run (count, stage 1, one per multiplicity, recheck).
 constexpr int FAST_LAUNCHES = 2 + NBUCKET + 1;

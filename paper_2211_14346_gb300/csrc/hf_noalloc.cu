@@ -80,7 +80,7 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
     if (n_events > NA_MAX_EVENTS)
         return set_error(HF_EINVAL, "hf_run_device_noalloc: more than HF_NOALLOC_MAX_EVENTS events; "
                                     "split the chunk or use hf_run_device");
-    if (n_variations < 1 || n_variations > 65535) return set_error(HF_EINVAL, "n_variations must be 1..65535");
+    if (n_variations < 1 || n_variations > HF_MAX_VARIATIONS) return set_error(HF_EINVAL, "n_variations must be 1..4096");
     if (n_events > 0 && (!dev_cols->jet_off || !dev_cols->btag || !dev_cols->lep || !dev_cols->lep_q ||
                          !dev_cols->met || (dev_cols->n_jets_total > 0 && !dev_cols->jets)))
         return set_error(HF_EINVAL, "a column pointer is NULL");

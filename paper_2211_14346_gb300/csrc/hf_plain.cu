@@ -20,7 +20,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
 {
     constexpr int NT = ntri(N);
     SemiEvent<N> se;
-    float g[N > 0 ? N * N : 1];
+    float g[NT > 0 ? NT : 1];
     float4 jet[N > 0 ? N : 1];
     const uint32_t j0 = C.jet_off[e];
 #pragma unroll
@@ -28,7 +28,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int i = 0; i <= j; ++i) g[i * N + j] = g[j * N + i] = minkowski_dot2(jet[i], jet[j]);
+        for (int i = 0; i <= j; ++i) g[tri(i, j)] = minkowski_dot2(jet[i], jet[j]);
     if (NT == 0) g[0] = 0.f;
     se.g = g;
     se.lep = C.lep[e];
@@ -75,46 +75,7 @@ __device__ __forceinline__ void plain_dispatch(int n, const Plan& P, const Cols&
     if constexpr (N > 0) plain_dispatch<N - 1>(n, P, C, O, S, e, V, seed, first_id, bits, fc, hist);
 }
 
-// Dilepton event in the plain form: jets read from global memory.
-__device__ __noinline__ void plain_dilep_event(const Plan& P, const Cols& C, const Out& O, const Scratch& S,
-                                               uint32_t e, int n, uint32_t V, uint64_t seed, uint64_t first_id,
-                                               unsigned bits, unsigned long long* fc, unsigned* hist)
-{
-    float4 jet[MAX_JETS];
-    const uint32_t j0 = C.jet_off[e];
-    for (int i = 0; i < n; ++i) jet[i] = C.jets[j0 + i];
-    const float4 l1 = C.lep[2 * (uint64_t)e], l2 = C.lep[2 * (uint64_t)e + 1];
-    const float2 met = C.met[e];
-    const unsigned btag = C.btag[e];
-    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
-    unsigned cnt = 0;
-    int nflag = 0;
-    uint16_t vs[64];
-    for (uint32_t v = 0; v < V; ++v) {
-        UnitOut r = dilep_unit_f(P, P.exec2, P.n_exec2, jet, n, btag, l1, l2, met, bits, first_id + e, v, seed);
-        if (r.f < 0) {
-            if (nflag < 64) {
-                vs[nflag++] = (uint16_t)v;
-                continue;
-            }
-            float4 reco;
-            int bin = 0;
-            r.f = unit_fp64(P, C, e, first_id + e, seed, v, bits, &reco, &bin);
-            r.reco = reco;
-            r.bin = bin;
-            atomicAdd(O.rc_total, 1ull);
-        }
-        atomicAdd(&fc[r.f], 1ull);
-        if (r.f == P.n_cuts) {
-            ++cnt;
-            atomicAdd(&hist[r.bin], 1u);
-            acc4(sum, comp, r.reco);
-        }
-    }
-    if (nflag == 0) write_event(O, e, cnt, sum, comp);
-    else pend_event(P, C, O, S, e, first_id + e, seed, bits, cnt, sum, comp, vs, nflag, fc, hist);
-}
-
+// Semileptonic model (the dilepton plain kernel is in hf_plain_dilep.cu).
 __global__ void __launch_bounds__(BLOCK) k_plain(const Plan P, const Cols C, uint32_t N, uint32_t V,
                                                  const Out O, Scratch S, uint64_t seed, uint64_t first_id)
 {
@@ -137,10 +98,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain(const Plan P, const Cols C, uin
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
                 write_zero_event(O, e);
             } else {
-                if (P.model == MODEL_DILEP)
-                    plain_dilep_event(P, C, O, S, e, (int)n, V, seed, first_id, bits, s_fc, s_hist);
-                else
-                    plain_dispatch<MAX_JETS>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);
+                plain_dispatch<MAX_JETS>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);
             }
         }
     }
@@ -152,6 +110,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain(const Plan P, const Cols C, uin
 cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                          uint64_t seed, uint64_t first_id, cudaStream_t st)
 {
+    if (P.model == MODEL_DILEP) return launch_plain_dilep(P, C, N, V, O, S, seed, first_id, st);
     k_plain<<<(N + BLOCK - 1) / BLOCK, BLOCK, 0, st>>>(P, C, N, V, O, S, seed, first_id);
     return cudaGetLastError();
 }

@@ -1,22 +1,24 @@
-// hf_s2_semi_a.cu -- instantiations of the semileptonic stage-2 kernel for
-// jet multiplicities 0, 1, 2, 3, 4, 5, 6, 7.
+// hf_s2_semi_a.cu -- instantiations of the semileptonic stage-2 kernels (single
+// chunk and batched) for jet multiplicities 0, 1, 2, 3, 4, 5.
 #include "hf_stage2_semi.cuh"
 
 namespace hf {
 template cudaError_t launch_s2_semi<0>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<0>(const BatchDev*, size_t, int, cudaStream_t);
 template cudaError_t launch_s2_semi<1>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<1>(const BatchDev*, size_t, int, cudaStream_t);
 template cudaError_t launch_s2_semi<2>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<2>(const BatchDev*, size_t, int, cudaStream_t);
 template cudaError_t launch_s2_semi<3>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<3>(const BatchDev*, size_t, int, cudaStream_t);
 template cudaError_t launch_s2_semi<4>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<4>(const BatchDev*, size_t, int, cudaStream_t);
 template cudaError_t launch_s2_semi<5>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_s2_semi<6>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_s2_semi<7>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                          uint64_t, uint64_t, int, int, cudaStream_t);
+                                       uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<5>(const BatchDev*, size_t, int, cudaStream_t);
 }  // namespace hf

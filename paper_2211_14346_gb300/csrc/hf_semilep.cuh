@@ -55,11 +55,9 @@ __host__ __device__ constexpr int pair_j(int p)
 }
 __host__ __device__ constexpr int pair_i(int p) { return p - pair_j(p) * (pair_j(p) - 1) / 2; }
 
-// Row stride of the full symmetric Gram matrix of an event (shared memory).
-template <int N>
-struct GramLayout {
-    static constexpr int STRIDE = (N * N) | 1;  // odd: events fall in different banks
-};
+// Event stride of the packed Gram matrices of a tile (shared memory): odd, so
+// that lanes reading the same entry of different events hit different banks.
+__host__ __device__ constexpr int gram_stride(int n) { return ntri(n) | 1; }
 
 // Top-2 tracker of candidate chi2 values with the masses of the best.
 struct Top2 {
@@ -83,8 +81,8 @@ struct Top2 {
 };
 
 // Minimum and second minimum of the triplet chi2, clamped at `cap`, with the
-// masses of the minimising candidate.  gf: full symmetric Gram matrix
-// (row-major N x N), s: jet scales.  Only candidates with chi2 < cap can
+// masses of the minimising candidate.  gf: packed upper triangle of the Gram
+// matrix (entry (i, j), i <= j, at tri(i, j)), s: jet scales.  Only candidates with chi2 < cap can
 // change any output (cap lies above the cut threshold by more than the error
 // bands, so a clamped minimum still decides the cut and the argmin gap
 // exactly).  Pairs and b-jets are fully unrolled for the multiplicity N: the
@@ -104,11 +102,11 @@ __device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict_
         float a[N];
         float q2[N * N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), gf[i * N + i]);
+        for (int i = 0; i < N; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), gf[tri(i, i)]);
 #pragma unroll
         for (int j = 1; j < N; ++j)
 #pragma unroll
-            for (int i = 0; i < j; ++i) q2[i * N + j] = q2[j * N + i] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), gf[i * N + j]);
+            for (int i = 0; i < j; ++i) q2[i * N + j] = q2[j * N + i] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), gf[tri(i, j)]);
         const float c_t = -P.mt * P.inv_sigma_t;
         const float c_w = -P.mW * P.inv_sigma_W;
         Top2 ta{cap, cap, 0.0f, 0.0f};
@@ -243,7 +241,7 @@ static __device__ __noinline__ float w_pz_fp64(const Plan& P, float4 l, float2 m
 // Per-event inputs of a semileptonic unit.
 template <int N>
 struct SemiEvent {
-    const float* g;  // packed Gram matrix (shared memory, or local memory in the plain form)
+    const float* g;  // packed Gram matrix (shared memory, or registers in the plain form)
     float4 lep;
     float2 met;
     unsigned s1bits;

@@ -2,12 +2,18 @@
 // tiles of events bucketed by their number of b-tagged jets (the pairings
 // solved per unit grow as n_b (n_b - 1)), largest buckets first.  Per tile:
 // (A) the events' jets, leptons and MET are staged in shared memory, (B) each
-// thread evaluates units (event x variation) with the FP32 two-neutrino solver
-// carrying error bounds, (C) one thread per event reduces its surviving units
-// in variation order or registers its flagged units for the FP64 recheck.
+// thread evaluates units (event x variation) with the FP32/FP64 two-neutrino
+// solver carrying error bounds, (C) one thread per event reduces its
+// surviving units in variation order or registers its flagged units for the
+// FP64 recheck.
+//
+// k_stage2_dilep: the tiles of one chunk.  k_bstage2_dilep: the tiles of every
+// dilepton chunk of a batch (buckets of all chunks, largest n_b first; tile ->
+// chunk by binary search in the per-chunk tile prefix).
 #include "hf_common.cuh"
 #include "hf_dilep.cuh"
 #include "hf_kernels.h"
+#include "hf_stage2_semi.cuh"  // S2Acc, upper_chunk, load_plan
 
 namespace hf {
 
@@ -27,11 +33,6 @@ struct DlSmem {
     int* uf;         // [unit]
 };
 
-__host__ __device__ inline size_t dl_smem_bytes(int ev, int units)
-{
-    return (size_t)ev * (12 * 16 + 32 + 8 + 16) + (size_t)units * 20 + 64;
-}
-
 __device__ inline DlSmem dl_carve(char* p, int ev, int units)
 {
     DlSmem t;
@@ -47,30 +48,75 @@ __device__ inline DlSmem dl_carve(char* p, int ev, int units)
     return t;
 }
 
+// One tile: ne events (ents) of one chunk with all their variations.
+__device__ void dilep_tile(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
+                           uint64_t first_id, const uint2* ents, int ne, const DlSmem& sm, const int* exec,
+                           int nexec, S2Acc& acc)
+{
+    // A: stage the tile's events
+    for (int t = threadIdx.x; t < ne; t += blockDim.x) {
+        uint2 en = ents[t];
+        const uint32_t e = en.x;
+        sm.evid[t] = e;
+        sm.bits[t] = en.y;
+        const uint32_t j0 = C.jet_off[e];
+        sm.nj[t] = C.jet_off[e + 1] - j0;
+        sm.btag[t] = C.btag[e];
+        sm.lep[2 * t] = __ldg(&C.lep[2 * (uint64_t)e]);
+        sm.lep[2 * t + 1] = __ldg(&C.lep[2 * (uint64_t)e + 1]);
+        sm.met[t] = __ldg(&C.met[e]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne * MAX_JETS; t += blockDim.x) {
+        const int ev = t / MAX_JETS, j = t - ev * MAX_JETS;
+        if (j < (int)sm.nj[ev]) sm.jets[ev * MAX_JETS + j] = __ldg(&C.jets[C.jet_off[sm.evid[ev]] + j]);
+    }
+    __syncthreads();
+    // B: units
+    const int nu = ne * (int)V;
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+        const int ev = u / (int)V;
+        const uint32_t v = (uint32_t)(u - ev * (int)V);
+        UnitOut r = dilep_unit_f(P, exec, nexec, sm.jets + ev * MAX_JETS, (int)sm.nj[ev], sm.btag[ev],
+                                 sm.lep[2 * ev], sm.lep[2 * ev + 1], sm.met[ev], sm.bits[ev],
+                                 first_id + sm.evid[ev], v, seed);
+        sm.uf[u] = r.f;
+        sm.ureco[u] = r.reco;
+        warp_tally(P, r, acc.fc, acc.hist, &acc.st);
+    }
+    __syncthreads();
+    // C: per-event reduction
+    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, acc.fc, acc.hist);
+    __syncthreads();
+}
+
+}  // namespace
+
+size_t dl_smem_bytes(int ev, int units)
+{
+    return (size_t)ev * (12 * 16 + 32 + 8 + 16) + (size_t)units * 20 + 64;
+}
+
 int dl_ev_per_tile(uint32_t V)
 {
     int e = DL_UNITS_PER_TILE / (int)V;
     return e < 1 ? 1 : (e > 64 ? 64 : e);
 }
 
-}  // namespace
-
 __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols C, const Out O, Scratch S, uint32_t V,
                                                         uint64_t seed, uint64_t first_id, int ept)
 {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ unsigned s_base[16], s_fill[16], s_tiles[17];
-    __shared__ unsigned long long s_fc[MAX_CUTS + 1];
-    __shared__ unsigned s_hist[MAX_BINS + 2];
-    __shared__ CutStats s_st;
+    __shared__ S2Acc acc;
     __shared__ int s_exec[MAX_CUTS];
     __shared__ int s_nexec;
     __shared__ unsigned s_tile;
     if (threadIdx.x == 0) {
-        unsigned acc = 0;
+        unsigned a = 0;
         for (int b = 0; b < NBUCKET; ++b) {
-            s_base[b] = acc;
-            acc += S.nhist[b];
+            s_base[b] = a;
+            a += S.nhist[b];
             s_fill[b] = S.cursor[b];
         }
         unsigned t = 0;
@@ -81,15 +127,8 @@ __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols
         s_tiles[16] = t;
         s_nexec = S.exec2 ? S.n_exec2 : P.n_exec2;
         for (int x = 0; x < s_nexec; ++x) s_exec[x] = S.exec2 ? S.exec2[x] : P.exec2[x];
-        s_st.cands = 0;
     }
-    if (threadIdx.x <= MAX_CUTS) s_fc[threadIdx.x] = 0;
-    for (int b = threadIdx.x; b < P.nbins + 2; b += blockDim.x) s_hist[b] = 0;
-    if (threadIdx.x < MAX_CUTS) {
-        s_st.evaluated[threadIdx.x] = 0;
-        s_st.passed[threadIdx.x] = 0;
-        s_st.cost[threadIdx.x] = 0;
-    }
+    acc.zero();
     __syncthreads();
     DlSmem sm = dl_carve(smem_raw, ept, ept * (int)V);
     bool any = false;
@@ -104,53 +143,105 @@ __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols
         while (b > 0 && tile >= s_tiles[b - 1]) --b;
         const unsigned first = (tile - s_tiles[b]) * (unsigned)ept;
         const int ne = (int)min((unsigned)ept, s_fill[b] - first);
-        const uint2* ents = S.bucket + s_base[b] + first;
-        // A: stage the tile's events
-        for (int t = threadIdx.x; t < ne; t += blockDim.x) {
-            uint2 en = ents[t];
-            const uint32_t e = en.x;
-            sm.evid[t] = e;
-            sm.bits[t] = en.y;
-            const uint32_t j0 = C.jet_off[e];
-            sm.nj[t] = C.jet_off[e + 1] - j0;
-            sm.btag[t] = C.btag[e];
-            sm.lep[2 * t] = __ldg(&C.lep[2 * (uint64_t)e]);
-            sm.lep[2 * t + 1] = __ldg(&C.lep[2 * (uint64_t)e + 1]);
-            sm.met[t] = __ldg(&C.met[e]);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < ne * MAX_JETS; t += blockDim.x) {
-            const int ev = t / MAX_JETS, j = t - ev * MAX_JETS;
-            if (j < (int)sm.nj[ev]) sm.jets[ev * MAX_JETS + j] = __ldg(&C.jets[C.jet_off[sm.evid[ev]] + j]);
-        }
-        __syncthreads();
-        // B: units
-        const int nu = ne * (int)V;
-        for (int u = threadIdx.x; u < nu; u += blockDim.x) {
-            const int ev = u / (int)V;
-            const uint32_t v = (uint32_t)(u - ev * (int)V);
-            UnitOut r = dilep_unit_f(P, s_exec, s_nexec, sm.jets + ev * MAX_JETS, (int)sm.nj[ev], sm.btag[ev],
-                                     sm.lep[2 * ev], sm.lep[2 * ev + 1], sm.met[ev], sm.bits[ev],
-                                     first_id + sm.evid[ev], v, seed);
-            sm.uf[u] = r.f;
-            sm.ureco[u] = r.reco;
-            warp_tally(P, r, s_fc, s_hist, &s_st);
-        }
-        __syncthreads();
-        // C: per-event reduction
-        reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, s_fc, s_hist);
-        __syncthreads();
+        dilep_tile(P, C, O, S, V, seed, first_id, S.bucket + s_base[b] + first, ne, sm, s_exec, s_nexec, acc);
     }
     if (!any) return;
-    flush_cutflow(P, O, s_fc);
-    flush_hist(P, O, s_hist);
-    if (threadIdx.x < P.n_cuts && S.stats) {
-        const int c = threadIdx.x;
-        if (s_st.evaluated[c]) atomicAdd(&S.stats[c], (unsigned long long)s_st.evaluated[c]);
-        if (s_st.passed[c]) atomicAdd(&S.stats[MAX_CUTS + c], (unsigned long long)s_st.passed[c]);
-        if (s_st.cost[c]) atomicAdd(&S.stats[2 * MAX_CUTS + c], s_st.cost[c]);
+    acc.flush(P, O, S.stats);
+    if (S.prof && threadIdx.x == 0 && acc.st.cands) atomicAdd(&S.prof[PROF_PAIRINGS], acc.st.cands);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_bstage2_dilep(const BatchDev* __restrict__ Bp)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ S2Acc acc;
+    __shared__ __align__(8) Plan s_plan;
+    __shared__ int s_exec[MAX_CUTS];
+    __shared__ int s_nexec;
+    __shared__ unsigned s_seg[NBUCKET + 1];  // tile segments, largest n_b first
+    __shared__ unsigned s_tile, s_chunk, s_bucket, s_tg;
+    const BatchDev& B = *Bp;
+    const unsigned nc = B.n_chunks, ns = B.n_semi;
+    if (ns == nc) return;
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int b = NBUCKET - 1; b >= 0; --b) {
+            const unsigned* pre = B.tpre + (size_t)b * (nc + 1);
+            s_seg[b] = t;
+            t += pre[nc] - pre[ns];
+        }
+        s_seg[NBUCKET] = t;
     }
-    if (S.prof && threadIdx.x == 0 && s_st.cands) atomicAdd(&S.prof[PROF_PAIRINGS], s_st.cands);
+    acc.zero();
+    __syncthreads();
+    const unsigned total = s_seg[NBUCKET];
+    if (total == 0) return;
+    int cur = -1;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const unsigned t = atomicAdd(&B.tctr[15], 1u);
+            s_tile = t;
+            if (t < total) {
+                int b = NBUCKET - 1;
+                while (b > 0 && t >= s_seg[b - 1]) --b;
+                const unsigned* pre = B.tpre + (size_t)b * (nc + 1);
+                const unsigned tg = t - s_seg[b] + pre[ns];  // tile index in the bucket's prefix
+                const unsigned c = upper_chunk(pre, ns, nc, tg);
+                s_bucket = (unsigned)b;
+                s_chunk = c;
+                s_tg = tg - pre[c];  // tile within the chunk's bucket
+            }
+        }
+        __syncthreads();
+        if (s_tile >= total) break;
+        const int c = (int)s_chunk;
+        const int b = (int)s_bucket;
+        const unsigned tl = s_tg;
+        const BChunk& ch = B.ch[c];
+        if (c != cur) {
+            if (cur >= 0) {
+                const BChunk& pc = B.ch[cur];
+                acc.flush(s_plan, pc.O, B.stats + (size_t)pc.plan * 3 * MAX_CUTS);
+                __syncthreads();
+                acc.zero();
+            }
+            load_plan(&s_plan, &B.plans[ch.plan]);
+            if (threadIdx.x == 0) {
+                s_nexec = B.plans[ch.plan].n_exec2;
+                const int* ex = B.exec[ch.plan];
+                for (int x = 0; x < s_nexec; ++x) s_exec[x] = ex[x];
+            }
+            cur = c;
+            __syncthreads();
+        }
+        const unsigned ept = ch.ept;
+        unsigned base = 0;
+        for (int k = 0; k < b; ++k) base += ch.cnt[k];
+        const unsigned first = tl * ept;
+        const int ne = (int)min(ept, ch.cnt[16 + b] - first);
+        Scratch S = B.S;
+        S.chunk = (uint32_t)c;
+        DlSmem sm = dl_carve(smem_raw, (int)ept, (int)(ept * ch.V));
+        dilep_tile(s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first, ne, sm,
+                   s_exec, s_nexec, acc);
+    }
+    if (cur >= 0) {
+        const BChunk& pc = B.ch[cur];
+        acc.flush(s_plan, pc.O, B.stats + (size_t)pc.plan * 3 * MAX_CUTS);
+    }
+}
+
+cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bstage2_dilep, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr = true;
+    }
+    int bs = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_dilep, BLOCK, smem);
+    if (bs < 1) bs = 1;
+    k_bstage2_dilep<<<sms * bs, BLOCK, smem, st>>>(B);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
@@ -158,6 +249,11 @@ cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Sc
 {
     const int ept = dl_ev_per_tile(V);
     const size_t smem = dl_smem_bytes(ept, ept * (int)V);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_stage2_dilep, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr = true;
+    }
     int bs = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_dilep, BLOCK, smem);
     if (bs < 1) bs = 1;

@@ -1,15 +1,20 @@
-// hf_stage2_semi.cuh -- stage-2 kernel of the semileptonic model for one
+// hf_stage2_semi.cuh -- stage-2 kernels of the semileptonic model for one
 // jet multiplicity N (instantiated per N in separate translation units so
 // that each gets its own register allocation and the build runs in parallel).
 //
-// Persistent grid over the tiles of bucket N: a tile is up to ev_per_tile
-// events of the bucket with all their variations.  Per tile: (A) the jets,
-// lepton and MET of its events are staged in shared memory and each event's
-// Gram matrix is computed once (compensated FP32), (B) every unit is
+// A tile is up to `ept` events of bucket N of one chunk with all their
+// variations.  Per tile: (A) the lepton and MET of its events are staged in
+// shared memory and each event's packed Gram matrix is computed once
+// (compensated FP32) from the jets in global memory, (B) every unit is
 // evaluated in FP32 registers (Philox smearing, MET cut, triplet chi2, W p_z)
 // with error bands, (C) one thread per event reduces its surviving units in
 // variation order and writes the event's outputs, or registers its flagged
 // units for the FP64 recheck.
+//
+// k_stage2_semi<N>: persistent grid over the tiles of one chunk.
+// k_bstage2_semi<N>: persistent grid over the tiles of every semileptonic
+// chunk of a batch (a device work queue: one atomic tile counter per
+// multiplicity, tile -> chunk by binary search in the per-chunk tile prefix).
 #pragma once
 #include "hf_common.cuh"
 #include "hf_semilep.cuh"
@@ -21,14 +26,7 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
                           const int* exec, int nexec, unsigned long long* fc, unsigned* hist, CutStats* st)
 {
-    // A: stage jets / lepton / MET, then the Gram matrices
-    if constexpr (N > 0) {
-        for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
-            int ev = t / N, j = t - ev * N;
-            uint32_t e = ents[ev].x;
-            sm.jets[ev * 12 + j] = __ldg(&C.jets[C.jet_off[e] + j]);
-        }
-    }
+    // A: stage lepton / MET, then the packed Gram matrices
     for (int t = threadIdx.x; t < ne; t += blockDim.x) {
         uint2 en = ents[t];
         sm.evid[t] = en.x;
@@ -38,16 +36,15 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
     }
     __syncthreads();
     constexpr int NT = ntri(N);
-    constexpr int GST = GramLayout<N>::STRIDE;
+    constexpr int GST = gram_stride(N);
     if constexpr (NT > 0) {
         for (int t = threadIdx.x; t < ne * NT; t += blockDim.x) {
             int ev = t / NT, k = t - ev * NT;
             int j = 0;
             while ((j + 1) * (j + 2) / 2 <= k) ++j;
             int i = k - j * (j + 1) / 2;
-            const float g = minkowski_dot2(sm.jets[ev * 12 + i], sm.jets[ev * 12 + j]);
-            sm.G[ev * GST + i * N + j] = g;
-            sm.G[ev * GST + j * N + i] = g;
+            const uint32_t j0 = __ldg(&C.jet_off[sm.evid[ev]]);
+            sm.G[ev * GST + k] = minkowski_dot2(__ldg(&C.jets[j0 + i]), __ldg(&C.jets[j0 + j]));
         }
     }
     __syncthreads();
@@ -73,38 +70,60 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
     __syncthreads();
 }
 
+// Block-level accumulators of the stage-2 kernels (shared memory).
+struct S2Acc {
+    unsigned long long fc[MAX_CUTS + 1];
+    unsigned hist[MAX_BINS + 2];
+    CutStats st;
+    __device__ void zero()
+    {
+        if (threadIdx.x <= MAX_CUTS) fc[threadIdx.x] = 0;
+        for (int b = threadIdx.x; b < MAX_BINS + 2; b += blockDim.x) hist[b] = 0;
+        if (threadIdx.x < MAX_CUTS) {
+            st.evaluated[threadIdx.x] = 0;
+            st.passed[threadIdx.x] = 0;
+            st.cost[threadIdx.x] = 0;
+        }
+        if (threadIdx.x == 0) st.cands = 0;
+    }
+    // Adds the block's counts to the chunk's cut flow and histogram and to the
+    // scheduler statistics (stats may be null).
+    __device__ void flush(const Plan& P, const Out& O, unsigned long long* stats)
+    {
+        flush_cutflow(P, O, fc);
+        flush_hist(P, O, hist);
+        if (threadIdx.x < P.n_cuts && stats) {
+            int c = threadIdx.x;
+            if (st.evaluated[c]) atomicAdd(&stats[c], (unsigned long long)st.evaluated[c]);
+            if (st.passed[c]) atomicAdd(&stats[MAX_CUTS + c], (unsigned long long)st.passed[c]);
+            if (st.cost[c]) atomicAdd(&stats[2 * MAX_CUTS + c], st.cost[c]);
+        }
+    }
+};
+
 template <int N>
 __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
                                                        int ev_per_tile)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    __shared__ unsigned long long s_fc[MAX_CUTS + 1];
-    __shared__ unsigned s_hist[MAX_BINS + 2];
-    __shared__ CutStats s_st;
+    __shared__ S2Acc acc;
     __shared__ int s_exec[MAX_CUTS];
     __shared__ int s_nexec;
     __shared__ unsigned s_tile, s_base, s_fill;
     if (threadIdx.x == 0) {
-        unsigned acc = 0;
-        for (int b = 0; b < N; ++b) acc += S.nhist[b];
-        s_base = acc;
+        unsigned a = 0;
+        for (int b = 0; b < N; ++b) a += S.nhist[b];
+        s_base = a;
         s_fill = S.cursor[N];
         s_nexec = S.exec2 ? S.n_exec2 : P.n_exec2;
         for (int x = 0; x < s_nexec; ++x) s_exec[x] = S.exec2 ? S.exec2[x] : P.exec2[x];
     }
-    if (threadIdx.x <= MAX_CUTS) s_fc[threadIdx.x] = 0;
-    for (int b = threadIdx.x; b < P.nbins + 2; b += blockDim.x) s_hist[b] = 0;
-    if (threadIdx.x < MAX_CUTS) {
-        s_st.evaluated[threadIdx.x] = 0;
-        s_st.passed[threadIdx.x] = 0;
-        s_st.cost[threadIdx.x] = 0;
-    }
-    if (threadIdx.x == 0) s_st.cands = 0;
+    acc.zero();
     __syncthreads();
     if (s_fill == 0) return;
     const unsigned ntiles = (s_fill + ev_per_tile - 1) / ev_per_tile;
-    TileSmem sm = carve(smem_raw, ev_per_tile, ev_per_tile * (int)V);
+    TileSmem sm = carve(smem_raw, ev_per_tile, ev_per_tile * (int)V, gram_stride(N));
     bool any = false;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&S.tile_ctr[N], 1u);
@@ -115,24 +134,98 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Pla
         any = true;
         unsigned first = tile * (unsigned)ev_per_tile;
         int ne = (int)min((unsigned)ev_per_tile, s_fill - first);
-        semi_tile<N>(P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec, s_fc,
-                     s_hist, &s_st);
+        semi_tile<N>(P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec, acc.fc,
+                     acc.hist, &acc.st);
     }
     if (!any) return;
-    flush_cutflow(P, O, s_fc);
-    flush_hist(P, O, s_hist);
-    if (threadIdx.x < P.n_cuts && S.stats) {
-        int c = threadIdx.x;
-        if (s_st.evaluated[c]) atomicAdd(&S.stats[c], (unsigned long long)s_st.evaluated[c]);
-        if (s_st.passed[c]) atomicAdd(&S.stats[MAX_CUTS + c], (unsigned long long)s_st.passed[c]);
-        if (s_st.cost[c]) atomicAdd(&S.stats[2 * MAX_CUTS + c], s_st.cost[c]);
-        if (S.prof && P.kind[c] == CUT_HADTOP_CHI2_MAX && s_st.evaluated[c])
-            atomicAdd(&S.prof[PROF_TOP + N], (unsigned long long)s_st.evaluated[c]);
-    }
-    if (S.prof && threadIdx.x == 0 && s_st.cands) atomicAdd(&S.prof[PROF_CANDS], s_st.cands);
+    acc.flush(P, O, S.stats);
+    if (threadIdx.x < P.n_cuts && S.prof && P.kind[threadIdx.x] == CUT_HADTOP_CHI2_MAX &&
+        acc.st.evaluated[threadIdx.x])
+        atomicAdd(&S.prof[PROF_TOP + N], (unsigned long long)acc.st.evaluated[threadIdx.x]);
+    if (S.prof && threadIdx.x == 0 && acc.st.cands) atomicAdd(&S.prof[PROF_CANDS], acc.st.cands);
     if (S.prof && threadIdx.x == 0 && blockIdx.x == 0) {
         atomicAdd(&S.prof[PROF_UNITS], (unsigned long long)s_fill * V);
         atomicAdd(&S.prof[PROF_EVENTS], (unsigned long long)s_fill);
+    }
+}
+
+// Largest c in [lo, hi) with pre[c] <= t (pre non-decreasing, pre[lo] <= t).
+__device__ __forceinline__ unsigned upper_chunk(const unsigned* pre, unsigned lo, unsigned hi, unsigned t)
+{
+    while (hi - lo > 1) {
+        unsigned mid = (lo + hi) / 2;
+        if (pre[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Copies a Plan into shared memory (all threads of the block).
+__device__ __forceinline__ void load_plan(Plan* dst, const Plan* src)
+{
+    const int* s = (const int*)src;
+    int* d = (int*)dst;
+    for (int i = threadIdx.x; i < (int)(sizeof(Plan) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const BatchDev* __restrict__ Bp)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ S2Acc acc;
+    __shared__ __align__(8) Plan s_plan;
+    __shared__ int s_exec[MAX_CUTS];
+    __shared__ int s_nexec;
+    __shared__ unsigned s_tile, s_chunk;
+    const BatchDev& B = *Bp;
+    const unsigned nc = B.n_chunks, ns = B.n_semi;
+    const unsigned* pre = B.tpre + (size_t)N * (nc + 1);
+    const unsigned total = pre[ns];
+    if (total == 0) return;
+    acc.zero();
+    int cur = -1;
+    while (true) {
+        if (threadIdx.x == 0) {
+            unsigned t = atomicAdd(&B.tctr[N], 1u);
+            s_tile = t;
+            if (t < total) s_chunk = upper_chunk(pre, 0, ns, t);
+        }
+        __syncthreads();
+        const unsigned t = s_tile;
+        const int c = (int)s_chunk;
+        if (t >= total) break;
+        const BChunk& ch = B.ch[c];
+        if (c != cur) {
+            if (cur >= 0) {
+                const BChunk& pc = B.ch[cur];
+                acc.flush(s_plan, pc.O, B.stats + (size_t)pc.plan * 3 * MAX_CUTS);
+                __syncthreads();
+                acc.zero();
+            }
+            load_plan(&s_plan, &B.plans[ch.plan]);
+            if (threadIdx.x == 0) {
+                s_nexec = B.plans[ch.plan].n_exec2;
+                const int* ex = B.exec[ch.plan];
+                for (int x = 0; x < s_nexec; ++x) s_exec[x] = ex[x];
+            }
+            cur = c;
+            __syncthreads();
+        }
+        const unsigned ept = ch.ept;
+        unsigned base = 0;
+        for (int b = 0; b < N; ++b) base += ch.cnt[b];
+        const unsigned fill = ch.cnt[16 + N];
+        const unsigned first = (t - pre[c]) * ept;
+        const int ne = (int)min(ept, fill - first);
+        Scratch S = B.S;
+        S.chunk = (uint32_t)c;
+        TileSmem sm = carve(smem_raw, (int)ept, (int)(ept * ch.V), gram_stride(N));
+        semi_tile<N>(s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first, ne, sm,
+                     s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
+    }
+    if (cur >= 0) {
+        const BChunk& pc = B.ch[cur];
+        acc.flush(s_plan, pc.O, B.stats + (size_t)pc.plan * 3 * MAX_CUTS);
     }
 }
 
@@ -141,7 +234,7 @@ template <int N>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
-    size_t smem = tile_smem_bytes(ept, ept * (int)V);
+    size_t smem = tile_smem_bytes(ept, ept * (int)V, gram_stride(N));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_stage2_semi<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -151,6 +244,22 @@ cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scr
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_semi<N>, BLOCK, smem);
     if (bs < 1) bs = 1;
     k_stage2_semi<N><<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
+    return cudaGetLastError();
+}
+
+// Batched form: smem = the largest tile of the batch at this multiplicity.
+template <int N>
+cudaError_t launch_bs2_semi(const BatchDev* B, size_t smem, int sms, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bstage2_semi<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr = true;
+    }
+    int bs = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_semi<N>, BLOCK, smem);
+    if (bs < 1) bs = 1;
+    k_bstage2_semi<N><<<sms * bs, BLOCK, smem, st>>>(B);
     return cudaGetLastError();
 }
 
