@@ -46,6 +46,11 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched"],
+                   help="semilep16: the headline (10M semileptonic events x 16 variations); "
+                        "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs")
+    p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
+    p.add_argument("--max-chunk", type=int, default=100000, help="batched: largest chunk (log-uniform from 1000)")
     return p.parse_args()
 
 
@@ -305,10 +310,103 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched chunks
+def batched_chunks(n_chunks, max_chunk, seed=4):
+    """Chunk list of the batched workload: sizes log-uniform over
+    [1000, max_chunk], event model semileptonic / dilepton 1:1, variations
+    drawn from {1, 8, 64}; each chunk is a contiguous slice of a device pool
+    of its model at a random offset, with its own global event ids."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(1000), np.log(max_chunk), n_chunks)).astype(np.int64)
+    models = rng.integers(0, 2, n_chunks)
+    Vs = rng.choice([1, 8, 64], n_chunks)
+    u = rng.random(n_chunks)
+    first = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    return [dict(n=int(n), model=int(m), V=int(v), u=float(x), first=int(f))
+            for n, m, v, x, f in zip(sizes, models, Vs, u, first)]
+
+
+def run_batched(a):
+    """Uneven chunks of both event models through hf_run_batch (one launch
+    sequence, replayed from its captured graph) against one plain
+    one-thread-per-event run per chunk, on the same device-resident slices."""
+    import numpy as np
+    import torch
+    import synth
+    from synth import analyses
+    from paper_2211_14346_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2211_14346_gb300 import Engine, DeviceColumns
+    spec = batched_chunks(a.chunks, a.max_chunk)
+    pool_n = max(c["n"] for c in spec)
+    pools = {0: DeviceColumns(synth.gen_semilep(max(pool_n, 4 * a.max_chunk), DATA_SEED)),
+             1: DeviceColumns(synth.gen_dilep(max(pool_n, 2 * a.max_chunk), 3))}
+    eng = Engine(0)
+    aids = {0: eng.define(analyses.config2()), 1: eng.define(analyses.config3())}
+    seeds = {0: SMEAR_SEED, 1: 1003}
+    items = []
+    for c in spec:
+        pool = pools[c["model"]]
+        lo = int(c["u"] * (pool.n_events - c["n"]))
+        items.append(dict(aid=aids[c["model"]], cols=pool.slice(lo, lo + c["n"]), V=c["V"], seed=seeds[c["model"]],
+                          first_event_id=c["first"]))
+    for it in items:
+        it["out"] = eng.results_for(it["aid"], it["cols"].n_events)
+    plain_out = [eng.results_for(it["aid"], it["cols"].n_events) for it in items]
+    n_events = sum(c["n"] for c in spec)
+    units = sum(c["n"] * c["V"] for c in spec)
+
+    def batched():
+        eng.run_batch(items)
+
+    def plain():
+        for it, o in zip(items, plain_out):
+            eng.run_device(it["aid"], it["cols"], V=it["V"], seed=it["seed"], first_event_id=it["first_event_id"],
+                           out=o, plain=True)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clk = ClockSampler(0)
+    clk.start()
+    ms_b = timed(batched, a.steps, a.warmup)
+    clocks = clk.stop()
+    ms_p = timed(plain, max(1, a.steps // 3), 1)
+    same = all(np.array_equal(it["out"].numpy()["cutflow"], o.numpy()["cutflow"]) and
+               np.array_equal(it["out"].numpy()["mask"], o.numpy()["mask"]) for it, o in zip(items, plain_out))
+    line = dict(metric="events/sec", value=n_events / (ms_b / 1e3), unit="events/s", n_gpus=1, steps=a.steps,
+                warmup=a.warmup, ms_per_step=ms_b, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="batched_uneven_chunks", chunks=len(spec), events=n_events, units=units,
+                            chunk_sizes="log-uniform [1000, %d]" % a.max_chunk, models="semilep:dilep 1:1",
+                            variations="{1, 8, 64}", semilep_events=sum(c["n"] for c in spec if c["model"] == 0),
+                            dilep_events=sum(c["n"] for c in spec if c["model"] == 1),
+                            l2="device-resident pools larger than L2; no flush"),
+                plain=dict(value=n_events / (ms_p / 1e3), ms_per_step=ms_p,
+                           note="one hf_run_device_plain per chunk (one thread per event)"),
+                speedup_vs_plain=ms_p / ms_b, identical_results=bool(same), clocks=clocks,
+                gpu_launches=int(6 + 13 + 1 + 2))
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_ours(a)
 

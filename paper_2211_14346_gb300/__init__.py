@@ -67,6 +67,7 @@ class DeviceColumns:
         self.lep = t(cols.lep)
         self.lep_q = t(cols.lep_q)
         self.met = t(cols.met)
+        self._off_host = np.asarray(cols.jet_off, dtype=np.int64)
 
     def struct(self):
         return columns_struct([x.data_ptr() for x in (self.jet_off, self.jets, self.btag, self.lep,
@@ -75,6 +76,24 @@ class DeviceColumns:
     def nbytes(self):
         return sum(x.numel() * x.element_size() for x in (self.jet_off, self.jets, self.btag, self.lep,
                                                            self.lep_q, self.met))
+
+    def slice(self, lo, hi):
+        """Events [lo, hi) as a chunk that shares this chunk's device memory
+        (only its rebased jet offsets are a new tensor)."""
+        out = DeviceColumns.__new__(DeviceColumns)
+        L = 1 if self.model == 1 else 2
+        j0, j1 = int(self._off_host[lo]), int(self._off_host[hi])
+        out.model = self.model
+        out.n_events = hi - lo
+        out.n_jets_total = j1 - j0
+        out._off_host = self._off_host[lo:hi + 1] - j0
+        out.jet_off = (self.jet_off[lo:hi + 1] - j0).contiguous()
+        out.jets = self.jets[j0:j1]
+        out.btag = self.btag[lo:hi]
+        out.lep = self.lep[lo * L:hi * L]
+        out.lep_q = self.lep_q[lo * L:hi * L]
+        out.met = self.met[lo:hi]
+        return out
 
 
 class PinnedColumns:
