@@ -46,7 +46,10 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched"],
+    p.add_argument("--requests", type=int, default=600, help="served: number of requests per arrival rate")
+    p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
+    p.add_argument("--rates", default="0.5,0.9,1.2", help="served: arrival rates as fractions of measured capacity")
+    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched", "served"],
                    help="semilep16: the headline (10M semileptonic events x 16 variations); "
                         "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs")
     p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
@@ -401,12 +404,156 @@ def run_batched(a):
     eng.close()
 
 
+# ------------------------------------------------------------------ served requests
+def served_requests(n_req, max_req, seed=5):
+    """Request list of the served workload: sizes log-uniform over
+    [1000, max_req], semileptonic / dilepton 70 / 30, variations uniform in
+    1..64, each a contiguous slice of a pinned host pool of its model."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(1000), np.log(max_req), n_req)).astype(np.int64)
+    models = (rng.random(n_req) < 0.3).astype(int)
+    Vs = rng.integers(1, 65, n_req)
+    u = rng.random(n_req)
+    first = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    return [dict(n=int(n), model=int(m), V=int(v), u=float(x), first=int(f))
+            for n, m, v, x, f in zip(sizes, models, Vs, u, first)]
+
+
+def run_served(a):
+    """Open-loop Poisson arrivals of analysis requests through hf_submit_chunk
+    with continuous batching (HF_FLAG_BATCHING): capacity from a closed-loop
+    pass, then arrival rates as fractions of it; latency = arrival to results
+    fetchable (admission waits included)."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    import synth
+    from synth import analyses
+    from paper_2211_14346_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2211_14346_gb300 import (Engine, PinnedColumns, columns_struct, _lib, HF_FLAG_BATCHING, HF_STATE_DONE,
+                                        HF_STATE_FAILED)
+    spec = served_requests(a.requests, a.max_request)
+    pool_n = max(c["n"] for c in spec)
+    pools = {0: PinnedColumns(synth.gen_semilep(max(2 * pool_n, 1000000), DATA_SEED)),
+             1: PinnedColumns(synth.gen_dilep(max(2 * pool_n, 500000), 3))}
+    offs = {k: np.asarray(p.jet_off.numpy(), dtype=np.int64) for k, p in pools.items()}
+    # per request: host column pointers into the pool and rebased offsets in pinned memory
+    off_buf = torch.empty(sum(c["n"] + 1 for c in spec), dtype=torch.int32).pin_memory()
+    ob = off_buf.numpy()
+    pos = 0
+    for c in spec:
+        pool, off = pools[c["model"]], offs[c["model"]]
+        lo = int(c["u"] * (pool.n_events - c["n"]))
+        hi = lo + c["n"]
+        L = 1 if c["model"] == 0 else 2
+        j0, j1 = int(off[lo]), int(off[hi])
+        ob[pos:pos + c["n"] + 1] = off[lo:hi + 1] - j0
+        ptrs = [off_buf.data_ptr() + 4 * pos, pool.jets.data_ptr() + 16 * j0, pool.btag.data_ptr() + 2 * lo,
+                pool.lep.data_ptr() + 16 * L * lo, pool.lep_q.data_ptr() + L * lo, pool.met.data_ptr() + 8 * lo]
+        c["cols"] = columns_struct(ptrs, j1 - j0)
+        pos += c["n"] + 1
+    eng = Engine(0, flags=HF_FLAG_BATCHING, hbm_budget_bytes=80 << 30, max_inflight=4096)
+    aids = {0: eng.define(analyses.config2()), 1: eng.define(analyses.config3())}
+    seeds = {0: SMEAR_SEED, 1: 1003}
+    n_cuts = {k: len(an["cuts"]) for k, an in ((0, analyses.config2()), (1, analyses.config3()))}
+    lib = eng.lib
+
+    def submit(c):
+        t = C.c_uint64()
+        st = lib.hf_submit_chunk(eng.ctx, aids[c["model"]], C.byref(c["cols"]), c["n"], c["first"],
+                                 seeds[c["model"]], c["V"], C.byref(t))
+        return st, t.value
+
+    cf_buf = {k: np.zeros(n_cuts[k] + 1, np.uint64) for k in (0, 1)}
+
+    def fetch(c, t):
+        rs = _lib.hf_results()
+        rs.cutflow = cf_buf[c["model"]].ctypes.data
+        _lib.check(lib.hf_fetch_results(eng.ctx, t, C.byref(rs), 600000), eng.ctx)
+
+    def one_pass(rate_hz):
+        """rate_hz None = closed loop (all submitted as admission allows)."""
+        n = len(spec)
+        rng = np.random.default_rng(55)
+        arrive = np.cumsum(rng.exponential(1.0 / rate_hz, n)) if rate_hz else np.zeros(n)
+        done_t = np.zeros(n)
+        t0 = time.perf_counter()
+        outstanding = []  # (index, ticket)
+        i = 0
+        st_poll = C.c_int32()
+        refused = 0
+        while i < n or outstanding:
+            now = time.perf_counter() - t0
+            while i < n and arrive[i] <= now:
+                st, t = submit(spec[i])
+                if st == _lib.HF_EBUSY:
+                    refused += 1
+                    break  # admission: retry after completions
+                _lib.check(st, eng.ctx)
+                outstanding.append((i, t))
+                i += 1
+            still = []
+            for k, t in outstanding:
+                _lib.check(lib.hf_poll(eng.ctx, t, C.byref(st_poll)), eng.ctx)
+                if st_poll.value == HF_STATE_DONE:
+                    done_t[k] = time.perf_counter() - t0
+                    fetch(spec[k], t)
+                elif st_poll.value == HF_STATE_FAILED:
+                    raise RuntimeError("request %d failed" % k)
+                else:
+                    still.append((k, t))
+            outstanding = still
+            time.sleep(0.0002)
+        lat = (done_t - arrive) * 1e3
+        span = done_t.max() - (arrive.min() if rate_hz else 0.0)
+        ev = sum(c["n"] for c in spec)
+        return dict(p50_ms=float(np.percentile(lat, 50)), p95_ms=float(np.percentile(lat, 95)),
+                    p99_ms=float(np.percentile(lat, 99)), events_per_s=ev / span, requests_per_s=n / span,
+                    span_s=span, admission_refusals=refused)
+
+    one_pass(None)  # warm-up: builds, graph captures, pool growth
+    torch.cuda.synchronize()
+    p0 = eng.profile()
+    clk = ClockSampler(0)
+    clk.start()
+    cap = one_pass(None)
+    p1 = eng.profile()
+    rates = []
+    for f in [float(x) for x in a.rates.split(",")]:
+        r = one_pass(f * cap["requests_per_s"])
+        r["rate_fraction"] = f
+        r["arrival_hz"] = f * cap["requests_per_s"]
+        rates.append(r)
+    clocks = clk.stop()
+    p2 = eng.profile()
+    n_events = sum(c["n"] for c in spec)
+    headline = min(rates, key=lambda r: abs(r["rate_fraction"] - 0.9)) if rates else cap
+    line = dict(metric="events/sec", value=cap["events_per_s"], unit="events/s", n_gpus=1, steps=1 + len(rates),
+                warmup=1, ms_per_step=cap["span_s"] * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="served_requests", requests=len(spec), events=n_events,
+                            request_sizes="log-uniform [1000, %d]" % a.max_request, models="semilep:dilep 70:30",
+                            variations="uniform 1..64", hbm_budget_gb=80, batching="continuous (HF_FLAG_BATCHING)",
+                            l2="columns copied from pinned host memory per request"),
+                capacity=cap, rates=rates,
+                latency_at_0p9=dict(p50_ms=headline["p50_ms"], p95_ms=headline["p95_ms"], p99_ms=headline["p99_ms"]),
+                batches_capacity_pass=p1["batches"] - p0["batches"],
+                chunks_per_batch=(p1["batched_chunks"] - p0["batched_chunks"]) / max(1, p1["batches"] - p0["batches"]),
+                batches_total=p2["batches"], clocks=clocks)
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "served":
+        run_served(a)
     else:
         run_ours(a)
 

@@ -62,6 +62,10 @@ typedef struct hf_ctx hf_ctx;
 #define HF_FLAG_DEBUG_SYNC 4u /* synchronise after every launch and check errors           */
 #define HF_FLAG_OVERLAP 16u   /* run the per-multiplicity stage-2 kernels of a run on side
                                  streams so that they overlap (default: one after another)  */
+#define HF_FLAG_BATCHING 32u  /* continuous batching of hf_submit_chunk: a dispatcher thread
+                                 of the context launches all queued chunks as one batch
+                                 (hf_run_batch's kernels) whenever fewer than two batches are
+                                 unfinished; chunks arriving meanwhile join the next batch */
 
 typedef struct {
     int32_t device;            /* CUDA device ordinal                                   */
@@ -155,7 +159,14 @@ typedef struct {
     uint64_t* recheck_count; /* 1: units re-evaluated in FP64 (diagnostic)              */
 } hf_results;
 
-/* Asynchronous chunk submission.  host_cols are HOST pointers, caller-owned,
+/* Asynchronous chunk submission (the serving entry point).  Admission: the
+ * chunk's device bytes (columns, results and cut-flow state, which stay
+ * device-resident until fetched) must fit the context's HBM budget next to
+ * the chunks in flight, else HF_EBUSY (nothing enqueued; retry after a fetch).
+ * The columns are copied on the context's host-to-device stream, overlapping
+ * the chunks already computing.  Without HF_FLAG_BATCHING the chunk's run is
+ * enqueued at once on the compute stream; with it the chunk is QUEUED until
+ * the dispatcher launches it in the next batch.  host_cols are HOST pointers, caller-owned,
  * that must stay valid and unchanged until the ticket is DONE or FAILED
  * (the library copies them to the device, from pinned memory directly or via
  * its pinned staging).  first_event_id is the global id of event 0 (it keys
@@ -271,7 +282,9 @@ typedef struct {
     uint64_t units_top[16];   /* units that evaluated the triplet chi2, by n_jets   */
     uint64_t units_dilep[16]; /* units that evaluated the two-neutrino solve, by n_b */
     uint64_t pairings_dilep;  /* b-jet pairings solved                               */
-    uint64_t cands_top;       /* triplet candidates evaluated (after pair pruning)   */
+    uint64_t cands_top;       /* triplet candidates evaluated                        */
+    uint64_t batches;         /* batches launched by the dispatcher (HF_FLAG_BATCHING) */
+    uint64_t batched_chunks;  /* chunks in those batches                             */
 } hf_profile_data;
 
 /* Waits for the profiled runs, writes the totals into *out (host) and, if

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (HF_FLAG_DEBUG_SYNC, HF_FLAG_NO_SCHED, HF_FLAG_PLAIN, HF_FLAG_PROFILE, HF_FLAG_OVERLAP,  # noqa: F401
-                   HFError,
+                   HF_FLAG_BATCHING, HFError,
                    HF_STATE_DONE, HF_STATE_FAILED, HF_STATE_QUEUED, HF_STATE_RUNNING)
 
 N_RECO = 4
@@ -305,7 +305,8 @@ class Engine:
         return dict(runs=p.runs, ms_stage1=p.ms_stage1, ms_stage2=p.ms_stage2, ms_recheck=p.ms_recheck,
                     launches_stage2=p.launches_stage2, units_stage2=p.units_stage2,
                     events_stage2=p.events_stage2, units_top=list(p.units_top),
-                    units_dilep=list(p.units_dilep), pairings_dilep=p.pairings_dilep, cands_top=p.cands_top)
+                    units_dilep=list(p.units_dilep), pairings_dilep=p.pairings_dilep, cands_top=p.cands_top,
+                    batches=p.batches, batched_chunks=p.batched_chunks)
 
     def set_exec_order(self, aid, order):
         o = np.ascontiguousarray(order, dtype=np.int32)

@@ -26,6 +26,7 @@ HF_FLAG_NO_SCHED = 2
 HF_FLAG_DEBUG_SYNC = 4
 HF_FLAG_PROFILE = 8
 HF_FLAG_OVERLAP = 16
+HF_FLAG_BATCHING = 32
 
 HF_MODEL_SEMILEP = 1
 HF_MODEL_DILEP = 2
@@ -72,7 +73,8 @@ class hf_profile_data(C.Structure):
     _fields_ = [("runs", C.c_uint64), ("ms_stage1", C.c_double), ("ms_stage2", C.c_double),
                 ("ms_recheck", C.c_double), ("launches_stage2", C.c_uint64), ("units_stage2", C.c_uint64),
                 ("events_stage2", C.c_uint64), ("units_top", C.c_uint64 * 16), ("units_dilep", C.c_uint64 * 16),
-                ("pairings_dilep", C.c_uint64), ("cands_top", C.c_uint64)]
+                ("pairings_dilep", C.c_uint64), ("cands_top", C.c_uint64), ("batches", C.c_uint64),
+                ("batched_chunks", C.c_uint64)]
 
 
 _lib = None

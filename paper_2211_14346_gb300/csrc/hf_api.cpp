@@ -15,6 +15,8 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -195,6 +197,13 @@ struct Ticket {
     ResLayout R;
     cudaEvent_t done = nullptr;
     bool failed_launch = false;
+    // continuous batching (HF_FLAG_BATCHING): the dispatcher launches queued
+    // tickets together; `done` is then the batch's event, shared by its tickets
+    bool batched = false;
+    bool launched = false;
+    cudaEvent_t h2d = nullptr;  // host-to-device copies of the columns finished
+    hf_chunk ch{};              // device view of the chunk (columns, results)
+    size_t off_res = 0, off_cf = 0, off_hist = 0, off_rct = 0, off_err = 0;  // the ticket's results
 };
 
 }  // namespace
@@ -223,9 +232,16 @@ struct hf_ctx {
     char* bstage = nullptr;
     size_t bstage_bytes = 0;
     cudaEvent_t bstage_free = nullptr;  // last upload from the staging buffer
-    cudaStream_t s_cap = nullptr;       // capture stream of the batch graph
-    cudaGraphExec_t bgraph = nullptr;
-    std::vector<uint64_t> bgraph_key;
+    cudaStream_t s_cap = nullptr;       // capture stream of the batch graphs
+    std::map<std::vector<uint64_t>, cudaGraphExec_t> bgraphs;  // captured launch sequences by shape
+    // continuous batching (HF_FLAG_BATCHING)
+    std::thread dispatcher;
+    std::condition_variable cv;
+    bool stop = false;
+    std::deque<uint64_t> pending;               // submitted, not yet launched
+    std::deque<cudaEvent_t> batches;            // done events of launched batches, oldest first
+    std::map<cudaEvent_t, int> done_refs;       // tickets still holding a batch's done event
+    uint64_t n_batches = 0, n_batched_tickets = 0;
     // profiling (HF_FLAG_PROFILE)
     unsigned long long* prof_dev = nullptr;  // u64[64] device counters
     std::vector<std::array<cudaEvent_t, 4>> prof_events;  // phases of runs not yet summed
@@ -233,6 +249,11 @@ struct hf_ctx {
 };
 
 namespace {
+
+hf_status submit_batched(hf_ctx* ctx, uint32_t analysis_id, const Analysis& A, const hf_columns* hc, uint64_t N,
+                         uint64_t first_event_id, uint64_t seed, uint32_t V, uint64_t* ticket);
+void dispatcher_main(hf_ctx* ctx);
+void release_done(hf_ctx* ctx, cudaEvent_t ev);
 
 // Chooses the device for the calling thread.
 hf_status use_device(hf_ctx* ctx)
@@ -358,11 +379,8 @@ hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
         ctx->arena = nullptr;
         ctx->arena_bytes = 0;
     }
-    if (ctx->bgraph) {  // captured for the old arena
-        cudaGraphExecDestroy(ctx->bgraph);
-        ctx->bgraph = nullptr;
-        ctx->bgraph_key.clear();
-    }
+    for (auto& g : ctx->bgraphs) cudaGraphExecDestroy(g.second);  // captured for the old arena
+    ctx->bgraphs.clear();
     size_t want = std::max(bytes, (size_t)64 << 20);
     cudaError_t e = cudaMalloc((void**)&ctx->arena, want);
     if (e != cudaSuccess) {
@@ -517,6 +535,7 @@ hf_status hf_open(const hf_config* cfg, hf_ctx** out)
         uint64_t thr = ctx->budget;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    if (ctx->flags & HF_FLAG_BATCHING) ctx->dispatcher = std::thread(dispatcher_main, ctx.get());
     *out = ctx.release();
     return HF_OK;
 }
@@ -524,6 +543,14 @@ hf_status hf_open(const hf_config* cfg, hf_ctx** out)
 hf_status hf_close(hf_ctx* ctx)
 {
     if (!ctx) return HF_OK;
+    if (ctx->dispatcher.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->stop = true;
+        }
+        ctx->cv.notify_all();
+        ctx->dispatcher.join();
+    }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);
@@ -540,11 +567,14 @@ hf_status hf_close(hf_ctx* ctx)
         }
         for (auto& kv : ctx->tickets) {
             if (kv.second.dmem) cudaFree(kv.second.dmem);
-            if (kv.second.done) cudaEventDestroy(kv.second.done);
+            if (kv.second.done && !kv.second.batched) cudaEventDestroy(kv.second.done);
         }
         for (auto& a : ctx->analyses)
             if (a->sched) cudaFree(a->sched);
-        if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+        for (auto& g : ctx->bgraphs) cudaGraphExecDestroy(g.second);
+        for (auto& d : ctx->done_refs) cudaEventDestroy(d.first);
+        for (auto& kv : ctx->tickets)
+            if (kv.second.h2d) cudaEventDestroy(kv.second.h2d);
         if (ctx->bstage) cudaFreeHost(ctx->bstage);
         if (ctx->bstage_free) cudaEventDestroy(ctx->bstage_free);
         if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
@@ -645,6 +675,7 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
     if (N > 0 && hc->jet_off[0] != 0) return fail(HF_EINVAL, "jet_off[0] must be 0");
     if (N > 0 && hc->jet_off[N] != hc->n_jets_total) return fail(HF_EINVAL, "jet_off[N] != n_jets_total");
     if (ctx->tickets.size() >= ctx->max_inflight) return fail(HF_EBUSY, "too many in-flight tickets");
+    if (ctx->flags & HF_FLAG_BATCHING) return submit_batched(ctx, analysis_id, *A, hc, N, first_event_id, seed, V, ticket);
     const uint64_t J = hc->n_jets_total;
     ColLayout CL = col_layout(N, J, L);
     RunLayout RL = layout_for(N, V);
@@ -712,6 +743,10 @@ hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state)
         *state = HF_STATE_FAILED;
         return HF_OK;
     }
+    if (it->second.batched && !it->second.launched) {
+        *state = HF_STATE_QUEUED;
+        return HF_OK;
+    }
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaEventQuery(it->second.done);
     if (e == cudaSuccess) *state = HF_STATE_DONE;
@@ -726,19 +761,24 @@ hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state)
 hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32_t timeout_ms)
 {
     if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
-    cudaEvent_t done;
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        auto it = ctx->tickets.find(ticket);
-        if (it == ctx->tickets.end()) return fail(HF_ENOTFOUND, "unknown ticket");
-        done = it->second.done;
-    }
     cudaSetDevice(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
-    while (true) {
-        cudaError_t e = cudaEventQuery(done);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the chunk");
+    while (true) {  // bounded wait: queued (batching) and then running
+        cudaEvent_t done = nullptr;
+        bool failed = false;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            auto it = ctx->tickets.find(ticket);
+            if (it == ctx->tickets.end()) return fail(HF_ENOTFOUND, "unknown ticket");
+            failed = it->second.failed_launch;
+            if (!it->second.batched || it->second.launched) done = it->second.done;
+        }
+        if (failed) break;
+        if (done) {
+            cudaError_t e = cudaEventQuery(done);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the chunk");
+        }
         if (std::chrono::steady_clock::now() - t0 >= std::chrono::milliseconds(timeout_ms))
             return fail(HF_ETIMEOUT, "chunk not finished within the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -750,36 +790,60 @@ hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32
     ctx->tickets.erase(it);
     ctx->inflight_bytes -= T.bytes;
     Analysis* A = get_analysis(ctx, T.analysis);
-    const int L = A->plan.model == MODEL_DILEP ? 2 : 1;
-    (void)L;
-    char* dscr = T.dmem + (T.bytes - T.L.scratch_bytes - T.R.bytes);
-    char* dres = dscr + T.L.scratch_bytes;
+    // where this ticket's results live
+    const char *d_err, *d_res, *d_cf, *d_hist, *d_rct;
+    if (T.batched) {
+        d_err = T.dmem + T.off_err;
+        d_res = T.dmem + T.off_res;
+        d_cf = T.dmem + T.off_cf;
+        d_hist = T.dmem + T.off_hist;
+        d_rct = T.dmem + T.off_rct;
+    } else {
+        const char* dscr = T.dmem + (T.bytes - T.L.scratch_bytes - T.R.bytes);
+        d_err = dscr + T.L.off_small + SM_ERR;
+        d_res = dscr + T.L.scratch_bytes;
+        d_cf = dscr + T.L.off_cutflow;
+        d_hist = dscr + T.L.off_hist;
+        d_rct = dscr + T.L.off_rctot;
+    }
     hf_status st = HF_OK;
     unsigned err = 0;
-    cudaError_t e = cudaMemcpy(&err, dscr + T.L.off_small + SM_ERR, 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) st = cuda_fail(e, "reading the error word");
+    cudaError_t e = cudaSuccess;
+    if (!T.failed_launch) {
+        e = cudaMemcpy(&err, d_err, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "reading the error word");
+    }
     if (!st && T.failed_launch) st = fail(HF_ECUDA, "the chunk's launch failed");
     if (!st && (err & ERR_COLUMNS)) st = fail(HF_EINVAL, "malformed columns (offsets or n_jets > 12)");
     if (!st && out) {
         const uint64_t N = T.N;
         const int nc = A->plan.n_cuts, nb = A->plan.nbins;
         cudaStream_t s = ctx->s_d2h;
-        if (out->mask && N) e = cudaMemcpyAsync(out->mask, dres + T.R.off_mask, N, cudaMemcpyDeviceToHost, s);
+        if (out->mask && N) e = cudaMemcpyAsync(out->mask, d_res + T.R.off_mask, N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->n_surv && N)
-            e = cudaMemcpyAsync(out->n_surv, dres + T.R.off_nsurv, 2 * N, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out->n_surv, d_res + T.R.off_nsurv, 2 * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->reco && N)
-            e = cudaMemcpyAsync(out->reco, dres + T.R.off_reco, 16 * N, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out->reco, d_res + T.R.off_reco, 16 * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->cutflow)
-            e = cudaMemcpyAsync(out->cutflow, dscr + T.L.off_cutflow, 8 * (nc + 1), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out->cutflow, d_cf, 8 * (nc + 1), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->hist)
-            e = cudaMemcpyAsync(out->hist, dscr + T.L.off_hist, 8 * (nb + 2), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out->hist, d_hist, 8 * (nb + 2), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->recheck_count)
-            e = cudaMemcpyAsync(out->recheck_count, dscr + T.L.off_rctot, 8, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out->recheck_count, d_rct, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "copying results");
     }
+    if (T.batched && !T.launched) {
+        // failed before launch: still queued copies may use the memory
+        cudaStreamSynchronize(ctx->s_h2d);
+    }
     cudaFreeAsync(T.dmem, ctx->s_d2h);
-    cudaEventDestroy(T.done);
+    if (T.batched) {
+        if (T.done) release_done(ctx, T.done);
+        if (T.h2d) cudaEventDestroy(T.h2d);
+    } else if (T.done) {
+        cudaEventDestroy(T.done);
+    }
     return st;
 }
 
@@ -846,7 +910,13 @@ hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset)
     if (!ctx || !out) return fail(HF_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (hf_status s = use_device(ctx)) return s;
-    if (!ctx->prof_dev) return fail(HF_ESTATE, "context not opened with HF_FLAG_PROFILE");
+    if (!ctx->prof_dev) {
+        if (!(ctx->flags & HF_FLAG_BATCHING)) return fail(HF_ESTATE, "context not opened with HF_FLAG_PROFILE");
+        memset(out, 0, sizeof *out);
+        out->batches = ctx->n_batches;
+        out->batched_chunks = ctx->n_batched_tickets;
+        return HF_OK;
+    }
     hf_profile_data& P = ctx->prof_acc;
     for (auto& ev : ctx->prof_events) {
         HF_CUDA(cudaEventSynchronize(ev[3]));
@@ -873,6 +943,8 @@ hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset)
         r.units_top[i] = cnt[PROF_TOP + i];
         r.units_dilep[i] = cnt[PROF_DILEP + i];
     }
+    r.batches = ctx->n_batches;
+    r.batched_chunks = ctx->n_batched_tickets;
     *out = r;
     if (reset) {
         memset(&ctx->prof_acc, 0, sizeof ctx->prof_acc);
@@ -895,13 +967,23 @@ struct BatchLayout {
 
 }  // namespace
 
-extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, void* stream)
+namespace {
+
+// Smallest power of two >= x (at least 4 KB): shared-memory sizes of the
+// stage-2 grids are rounded to these classes so that batches with similar
+// variation counts share one captured launch sequence.
+size_t smem_class(size_t x)
 {
-    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
-    if (n_chunks > 0 && !chunks) return fail(HF_EINVAL, "chunks is NULL");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (hf_status s = use_device(ctx)) return s;
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
+    size_t c = 4096;
+    while (c < x) c <<= 1;
+    return c;
+}
+
+// Enqueues one batch on st (ctx->mu held): validation, tables, upload and the
+// captured launch sequence (captured on first use of its shape).
+hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, cudaStream_t st,
+                        unsigned* const* errs = nullptr)
+{
     if (n_chunks == 0) return HF_OK;
     // validate; semileptonic chunks first (the kernels take each model's chunks as one range)
     std::vector<uint32_t> order;
@@ -967,18 +1049,20 @@ extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t 
         b.model = (uint32_t)P.model;
         b.blk0 = (uint32_t)blocks;
         b.ev0 = ev_total;
+        b.err = errs ? errs[order[x]] : nullptr;
         const uint64_t units = (uint64_t)b.n * b.V;
         if (P.model == MODEL_DILEP) {
             b.ept = (uint32_t)dl_ev_per_tile(b.V);
             BL.dilep = true;
-            BL.smem_dilep = std::max(BL.smem_dilep, dl_smem_bytes((int)b.ept, (int)(b.ept * b.V)));
+            BL.smem_dilep = std::max(BL.smem_dilep, smem_class(dl_smem_bytes((int)b.ept, (int)(b.ept * b.V))));
             units_dl += units;
         } else {
             b.ept = (uint32_t)ev_per_tile_for(b.V);
             ++n_semi;
             BL.semi_mask = (1u << NBUCKET) - 1;
             for (int n = 0; n < NBUCKET; ++n)
-                BL.smem_semi[n] = std::max(BL.smem_semi[n], semi_tile_bytes(n, (int)b.ept, (int)(b.ept * b.V)));
+                BL.smem_semi[n] = std::max(BL.smem_semi[n],
+                                           smem_class(semi_tile_bytes(n, (int)b.ept, (int)(b.ept * b.V))));
             units_semi += units;
         }
         ev_total += b.n;
@@ -1113,11 +1197,11 @@ extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t 
         key.push_back((uint64_t)(uintptr_t)A->sched);
         key.push_back(A->no_sched ? 1 : 0);
     }
-    if (!(ctx->bgraph && ctx->bgraph_key == key)) {
-        if (ctx->bgraph) {
-            cudaGraphExecDestroy(ctx->bgraph);
-            ctx->bgraph = nullptr;
-            ctx->bgraph_key.clear();
+    auto git = ctx->bgraphs.find(key);
+    if (git == ctx->bgraphs.end()) {
+        if (ctx->bgraphs.size() >= 32) {  // bounded cache of shapes
+            for (auto& g : ctx->bgraphs) cudaGraphExecDestroy(g.second);
+            ctx->bgraphs.clear();
         }
         if (!ctx->s_cap) HF_CUDA(cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking));
         HF_CUDA(cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal));
@@ -1132,17 +1216,169 @@ extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t 
             if (g) cudaGraphDestroy(g);
             return cuda_fail(e != cudaSuccess ? e : e2, "capturing the batch launch sequence");
         }
-        e = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            ctx->bgraph = nullptr;
-            return cuda_fail(e, "cudaGraphInstantiate(batch)");
-        }
-        ctx->bgraph_key = key;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+        git = ctx->bgraphs.emplace(key, ge).first;
     }
-    HF_CUDA(cudaGraphLaunch(ctx->bgraph, st));
+    HF_CUDA(cudaGraphLaunch(git->second, st));
     if (!ctx->arena_free) HF_CUDA(cudaEventCreateWithFlags(&ctx->arena_free, cudaEventDisableTiming));
     HF_CUDA(cudaEventRecord(ctx->arena_free, st));
     if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
     return HF_OK;
 }
+
+}  // namespace
+
+extern "C" hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, void* stream)
+{
+    if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    if (n_chunks > 0 && !chunks) return fail(HF_EINVAL, "chunks is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
+    return batch_enqueue(ctx, chunks, n_chunks, st);
+}
+
+// ------------------------------------------------------------------ continuous batching
+namespace {
+
+// hf_submit_chunk with HF_FLAG_BATCHING (ctx->mu held): admission by the HBM
+// budget, one allocation for the chunk's columns and results, the copies on
+// the H2D stream, and the ticket queued for the dispatcher.
+hf_status submit_batched(hf_ctx* ctx, uint32_t analysis_id, const Analysis& A, const hf_columns* hc, uint64_t N,
+                         uint64_t first_event_id, uint64_t seed, uint32_t V, uint64_t* ticket)
+{
+    const int L = A.plan.model == MODEL_DILEP ? 2 : 1;
+    const uint64_t J = hc->n_jets_total;
+    ColLayout CL = col_layout(N, J, L);
+    ResLayout RR = res_layout(N);
+    Ticket T;
+    T.off_res = CL.bytes;
+    T.off_cf = align_up(CL.bytes + RR.bytes, 256);
+    T.off_hist = T.off_cf + 8 * (MAX_CUTS + 1);
+    T.off_rct = T.off_hist + 8 * (MAX_BINS + 2);
+    T.off_err = T.off_rct + 8;
+    const size_t bytes = align_up(T.off_err + 4, 256);
+    if (ctx->inflight_bytes + bytes > ctx->budget) return fail(HF_EBUSY, "HBM budget exhausted; retry later");
+    T.id = ctx->next_ticket++;
+    T.analysis = analysis_id;
+    T.N = N;
+    T.bytes = bytes;
+    T.R = RR;
+    T.batched = true;
+    cudaError_t e = cudaMallocAsync((void**)&T.dmem, bytes, ctx->s_h2d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HF_ENOMEM, "device allocation for the chunk failed");
+    }
+    char* dc = T.dmem;
+    if (N > 0) {
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jets, hc->jets, 16 * J, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep, hc->lep, 16 * (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_met, hc->met, 8 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jet_off, hc->jet_off, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_btag, hc->btag, 2 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep_q, hc->lep_q, (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+    }
+    HF_CUDA(cudaMemsetAsync(dc + T.off_err, 0, 4, ctx->s_h2d));
+    HF_CUDA(cudaEventCreateWithFlags(&T.h2d, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(T.h2d, ctx->s_h2d));
+    hf_chunk& c = T.ch;
+    c.analysis_id = analysis_id;
+    c.n_variations = V;
+    c.n_events = N;
+    c.first_event_id = first_event_id;
+    c.seed = seed;
+    c.cols.jet_off = (const uint32_t*)(dc + CL.off_jet_off);
+    c.cols.jets = (const float*)(dc + CL.off_jets);
+    c.cols.btag = (const uint16_t*)(dc + CL.off_btag);
+    c.cols.lep = (const float*)(dc + CL.off_lep);
+    c.cols.lep_q = (const int8_t*)(dc + CL.off_lep_q);
+    c.cols.met = (const float*)(dc + CL.off_met);
+    c.cols.n_jets_total = J;
+    char* dres = dc + T.off_res;
+    c.out.mask = (uint8_t*)(dres + RR.off_mask);
+    c.out.n_surv = (uint16_t*)(dres + RR.off_nsurv);
+    c.out.reco = (float*)(dres + RR.off_reco);
+    c.out.cutflow = (uint64_t*)(dc + T.off_cf);
+    c.out.hist = (uint64_t*)(dc + T.off_hist);
+    c.out.recheck_count = (uint64_t*)(dc + T.off_rct);
+    ctx->inflight_bytes += bytes;
+    *ticket = T.id;
+    ctx->tickets[T.id] = T;
+    ctx->pending.push_back(T.id);
+    ctx->cv.notify_one();
+    return HF_OK;
+}
+
+// Drops one reference to a batch's done event (destroyed with the last).
+void release_done(hf_ctx* ctx, cudaEvent_t ev)
+{
+    auto it = ctx->done_refs.find(ev);
+    if (it == ctx->done_refs.end()) return;
+    if (--it->second == 0) {
+        cudaEventDestroy(ev);
+        ctx->done_refs.erase(it);
+    }
+}
+
+// The dispatcher of continuous batching: whenever chunks are queued and at
+// most one launched batch is still unfinished, it launches everything queued
+// (up to a size limit) as one batch after their copies; chunks that arrive
+// while batches run join the next one, and their copies overlap the running
+// batch.
+void dispatcher_main(hf_ctx* ctx)
+{
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    while (true) {
+        ctx->cv.wait(lk, [ctx] { return ctx->stop || !ctx->pending.empty(); });
+        if (ctx->stop) break;
+        while (true) {
+            while (!ctx->batches.empty() && cudaEventQuery(ctx->batches.front()) != cudaErrorNotReady) {
+                release_done(ctx, ctx->batches.front());
+                ctx->batches.pop_front();
+            }
+            if (ctx->batches.size() < 2 || ctx->stop) break;
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
+        }
+        if (ctx->stop) break;
+        std::vector<hf_chunk> chs;
+        std::vector<unsigned*> errs;
+        std::vector<uint64_t> ids;
+        uint64_t units = 0;
+        while (!ctx->pending.empty() && chs.size() < 4096 && units < (1ull << 31)) {
+            const uint64_t id = ctx->pending.front();
+            ctx->pending.pop_front();
+            auto it = ctx->tickets.find(id);
+            if (it == ctx->tickets.end()) continue;
+            Ticket& T = it->second;
+            cudaStreamWaitEvent(ctx->s_comp, T.h2d, 0);
+            chs.push_back(T.ch);
+            errs.push_back((unsigned*)(T.dmem + T.off_err));
+            ids.push_back(id);
+            units += T.ch.n_events * T.ch.n_variations;
+        }
+        if (chs.empty()) continue;
+        const hf_status st = batch_enqueue(ctx, chs.data(), (uint32_t)chs.size(), ctx->s_comp, errs.data());
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->s_comp);
+        ctx->done_refs[ev] = (int)ids.size() + 1;  // + the reference of ctx->batches
+        ctx->batches.push_back(ev);
+        for (uint64_t id : ids) {
+            Ticket& T = ctx->tickets[id];
+            T.launched = true;
+            T.done = ev;
+            if (st != HF_OK || e != cudaSuccess) T.failed_launch = true;
+        }
+        ++ctx->n_batches;
+        ctx->n_batched_tickets += ids.size();
+    }
+}
+
+}  // namespace

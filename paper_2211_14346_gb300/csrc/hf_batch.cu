@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(BLOCK1) k_bstage1(const BatchDev* __restrict__
             const uint32_t n = b - a;
             if (b < a || n > MAX_JETS || (uint64_t)b > ch.C.n_jets_total) {
                 atomicOr(B.S.err, ERR_COLUMNS);
+                if (ch.err) atomicOr(ch.err, ERR_COLUMNS);
                 write_zero_event(ch.O, e);
             } else {
                 bits = stage1_bits(P, ch.C, e, (int)n);

@@ -133,6 +133,7 @@ struct BChunk {
     uint32_t model;
     uint64_t ev0;      // first bucket slot of the chunk in the batch's bucket array
     unsigned* cnt;     // [32] nhist[16] | cursor[16] of the chunk
+    unsigned* err;     // the chunk's own error word, or null
 };
 
 constexpr int BLOCK1 = 256;  // events per stage-1 block
