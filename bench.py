@@ -49,9 +49,11 @@ def _args():
     p.add_argument("--requests", type=int, default=600, help="served: number of requests per arrival rate")
     p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
     p.add_argument("--rates", default="0.5,0.9,1.2", help="served: arrival rates as fractions of measured capacity")
-    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched", "served"],
+    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched", "served", "dilep", "unsmeared"],
                    help="semilep16: the headline (10M semileptonic events x 16 variations); "
-                        "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs")
+                        "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs; "
+                        "served: open-loop requests with continuous batching; dilep: 2M ttH-like dilepton events x 64; "
+                        "unsmeared: 10M semileptonic events, no smearing (the column-scan chain)")
     p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
     p.add_argument("--max-chunk", type=int, default=100000, help="batched: largest chunk (log-uniform from 1000)")
     return p.parse_args()
@@ -216,6 +218,7 @@ def run_ours(a):
     dc = DeviceColumns(cols)
     out = eng.results_for(aid, N)
     stream = torch.cuda.current_stream()
+    tuned = eng.autotune(aid, dc.slice(0, min(N, 1000000)), V=V, seed=SMEAR_SEED)  # tile shape, untimed
 
     def barrier():
         if dist is not None:
@@ -303,7 +306,8 @@ def run_ours(a):
                         smearing="jet energy x N(1, 0.10), MET + N(0, 10 GeV)", cuts=[c[0] for c in an["cuts"]],
                         l2="inputs (%.2f GB per GPU) larger than L2 (129 MB); no flush" % (dc.nbytes() / 1e9),
                         fp64_recheck_units_per_step=int(res["recheck_count"]),
-                        units_per_step=N * V, cutflow=[int(x) for x in res["cutflow"]]),
+                        units_per_step=N * V, cutflow=[int(x) for x in res["cutflow"]],
+                        units_per_tile=tuned),
             roofline=roof,
             cpu_baseline=cpu_base,
             e2e=e2e,
@@ -360,6 +364,11 @@ def run_batched(a):
         lo = int(c["u"] * (pool.n_events - c["n"]))
         items.append(dict(aid=aids[c["model"]], cols=pool.slice(lo, lo + c["n"]), V=c["V"], seed=seeds[c["model"]],
                           first_event_id=c["first"]))
+    tuned = {}
+    for m, pool in pools.items():  # tile shapes for every (model, variation count) of the batch
+        for v in (1, 8, 64):
+            tuned["%s_V%d" % ("semilep" if m == 0 else "dilep", v)] = eng.autotune(
+                aids[m], pool.slice(0, min(pool.n_events, 400000 if m == 0 else 100000)), V=v, seed=seeds[m])
     for it in items:
         it["out"] = eng.results_for(it["aid"], it["cols"].n_events)
     plain_out = [eng.results_for(it["aid"], it["cols"].n_events) for it in items]
@@ -404,7 +413,7 @@ def run_batched(a):
                             l2="device-resident pools larger than L2; no flush"),
                 plain=dict(value=n_events / (ms_p / 1e3), ms_per_step=ms_p,
                            note="one hf_run_device_plain per chunk (one thread per event)"),
-                speedup_vs_plain=ms_p / ms_b, identical_results=bool(same), clocks=clocks,
+                speedup_vs_plain=ms_p / ms_b, identical_results=bool(same), clocks=clocks, units_per_tile=tuned,
                 gpu_launches=int(6 + 13 + 1 + 2))
     print(json.dumps(line), flush=True)
     eng.close()
@@ -552,6 +561,78 @@ def run_served(a):
     eng.close()
 
 
+# ------------------------------------------------------------------ single-chunk workloads
+def run_single_workload(a):
+    """dilep: 2,000,000 ttH-like dilepton events x 64 variations (data seed 3,
+    Philox seed 1003); unsmeared: 10,000,000 semileptonic events, V = 1, no
+    smearing (data seed 2).  Device-resident columns; the plain
+    one-thread-per-event form timed beside it on the same data."""
+    import numpy as np
+    import torch
+    import synth
+    from synth import analyses
+    from paper_2211_14346_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2211_14346_gb300 import Engine, DeviceColumns, HF_FLAG_PROFILE
+    if a.workload == "dilep":
+        N = a.events if a.events != N_EVENTS else 2_000_000
+        cols, an, Vw, seed, name = synth.gen_dilep(N, 3), analyses.config3(), 64, 1003, "dilep_tth_2M_x64"
+    else:
+        N = a.events
+        cols, an, Vw, seed, name = synth.gen_semilep(N, DATA_SEED), analyses.config1(), 1, 0, "semilep_unsmeared_10M"
+    eng = Engine(0, flags=HF_FLAG_PROFILE)
+    aid = eng.define(an)
+    dc = DeviceColumns(cols)
+    out = eng.results_for(aid, N)
+    tuned = eng.autotune(aid, dc.slice(0, min(N, 1000000 if Vw == 1 else 50000)), V=Vw, seed=seed)
+
+    def timed(plain, steps, warmup):
+        for _ in range(warmup):
+            eng.run_device(aid, dc, V=Vw, seed=seed, out=out, plain=plain)
+        torch.cuda.synchronize()
+        eng.profile(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            eng.run_device(aid, dc, V=Vw, seed=seed, out=out, plain=plain)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, eng.profile(reset=True)
+
+    clk = ClockSampler(0)
+    clk.start()
+    ms, prof = timed(False, a.steps, a.warmup)
+    clocks = clk.stop()
+    res = out.numpy()
+    ms_plain, _ = timed(True, max(1, a.steps // 3), 1)
+    runs = max(1, prof["runs"])
+    line = dict(metric="events/sec", value=N / (ms / 1e3), unit="events/s", n_gpus=1, steps=a.steps, warmup=a.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic",
+                config=dict(workload=name, events=N, variations=Vw, cutflow=[int(x) for x in res["cutflow"]],
+                            fp64_recheck_units=int(res["recheck_count"]), units_per_tile=tuned,
+                            l2="inputs (%.2f GB) larger than L2; no flush" % (dc.nbytes() / 1e9)),
+                profile=dict(ms_stage1=prof["ms_stage1"] / runs, ms_stage2=prof["ms_stage2"] / runs,
+                             ms_recheck=prof["ms_recheck"] / runs, pairings=prof["pairings_dilep"] // runs),
+                plain=dict(value=N / (ms_plain / 1e3), ms_per_step=ms_plain), speedup_vs_plain=ms_plain / ms,
+                clocks=clocks)
+    if a.workload == "unsmeared":
+        # algorithmic bytes of the chain: each cut reads the columns it needs for the
+        # events that reach it (jet_off 4 B, b-tags 2 B, lepton pT 8 B, MET 8 B,
+        # lepton p_z and E 8 B, the event's jets 16 B each), plus the outputs
+        cf = res["cutflow"].astype(np.float64)
+        jets_c6 = sum(n * u for n, u in enumerate(prof["units_top"])) / runs
+        algo = 4 * N + 2 * cf[1] + 8 * cf[2] + 8 * cf[3] + 8 * cf[4] + 16 * jets_c6 + 19 * N
+        peak = 6783.8
+        line["roofline"] = dict(bound="hbm", achieved=algo / (ms / 1e3) / 1e9, peak=peak, unit="GB/s",
+                                frac=algo / (ms / 1e3) / 1e9 / peak, traffic=None,
+                                note="whole chain (all kernels of a step); measured copy peak; the triplet chi2 "
+                                     "of stage 2 makes the chain compute-bound")
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -560,6 +641,8 @@ def main():
         run_batched(a)
     elif a.workload == "served":
         run_served(a)
+    elif a.workload in ("dilep", "unsmeared"):
+        run_single_workload(a)
     else:
         run_ours(a)
 

@@ -247,6 +247,19 @@ typedef struct {
  * HF_ENOMEM, HF_ECUDA.  Malformed columns set the device error word. */
 hf_status hf_run_batch(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, void* stream);
 
+/* Autotuner of the stage-2 tile shape: runs the fast path on a sample of
+ * DEVICE columns (n_events >= 1, typically 10^5..10^6 events of the workload)
+ * with each candidate number of units per tile (semileptonic 128, 256, 512,
+ * 1024; dilepton 32, 64, 128, 256), timed with CUDA events on the context's
+ * stream after a warm-up run, and keeps the fastest for this analysis's event
+ * model and the variation class of n_variations (V = 1, 2-3, 4-7, ..., >= 128)
+ * in the context; later hf_run_device, hf_submit_chunk and hf_run_batch
+ * calls with that model and class use it.  *units_per_tile (may be NULL)
+ * receives the choice.  Synchronises the context's stream.
+ * Errors: HF_EINVAL, HF_ENOTFOUND, HF_ENOMEM, HF_ECUDA. */
+hf_status hf_autotune(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols, uint64_t n_events,
+                      uint32_t n_variations, uint64_t seed, int32_t* units_per_tile);
+
 /* Waits for the context's stream and returns the device error word of the
  * last hf_run_device* or hf_run_batch call in *word (0 = none; bit 0 = malformed offsets or
  * n_jets > 12).  Errors: HF_ECUDA. */

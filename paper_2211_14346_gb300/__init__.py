@@ -248,6 +248,14 @@ class Engine:
         self._check(self.lib.hf_run_batch(self.ctx, arr, len(items), stream))
         return outs
 
+    def autotune(self, aid, dcols, *, V=1, seed=0):
+        """Picks the stage-2 units per tile for this analysis's model and V's
+        class from timed runs on dcols (device columns); returns the choice."""
+        cs = dcols.struct()
+        k = C.c_int32()
+        self._check(self.lib.hf_autotune(self.ctx, aid, C.byref(cs), dcols.n_events, V, seed, C.byref(k)))
+        return k.value
+
     def device_error(self):
         w = C.c_uint32()
         self._check(self.lib.hf_device_error(self.ctx, C.byref(w)))

@@ -108,6 +108,7 @@ def load():
         "hf_run_device_noalloc": ([C.POINTER(hf_analysis_desc), C.POINTER(hf_columns), u64, u64, u64, u32,
                                    C.POINTER(hf_results), vp], i32),
         "hf_run_batch": ([vp, C.POINTER(hf_chunk), u32, vp], i32),
+        "hf_autotune": ([vp, u32, C.POINTER(hf_columns), u64, u32, u64, C.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -121,7 +122,7 @@ def declared_symbols():
     """Names of the entry points this binding marshals (the ones hf.h declares)."""
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
-            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch"]
+            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch", "hf_autotune"]
 
 
 class HFError(RuntimeError):

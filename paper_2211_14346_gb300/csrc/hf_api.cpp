@@ -217,6 +217,7 @@ struct hf_ctx {
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     cudaStream_t user_stream = nullptr;
     SideStreams side{};  // stage-2 kernels of one run overlap on these
+    int tune[3][8] = {};  // autotuned units per stage-2 tile by [model][variation class] (0 = default)
     std::mutex mu;
     std::vector<std::unique_ptr<Analysis>> analyses;
     // scratch arena for device-resident runs
@@ -249,6 +250,14 @@ struct hf_ctx {
 };
 
 namespace {
+
+// Variation class of the autotuner: 0 for V = 1, else floor(log2 V), at most 7.
+int vclass(uint32_t V)
+{
+    int c = 0;
+    while (c < 7 && (2u << c) <= V) ++c;
+    return V <= 1 ? 0 : c;
+}
 
 hf_status submit_batched(hf_ctx* ctx, uint32_t analysis_id, const Analysis& A, const hf_columns* hc, uint64_t N,
                          uint64_t first_event_id, uint64_t seed, uint32_t V, uint64_t* ticket);
@@ -417,7 +426,9 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
         for (auto& x : ev) HF_CUDA(cudaEventCreate(&x));
         evp = ev.data();
     }
-    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st, evp, &ctx->side));
+    const int upt = ctx->tune[A.plan.model == MODEL_DILEP ? 2 : 1][vclass(V)];
+    HF_CUDA(launch_run(A.plan, C, (uint32_t)N, V, O, S, seed, first_id, use_plain, ctx->sms, st, evp, &ctx->side,
+                       upt));
     if (evp) ctx->prof_events.push_back(ev);
     if (!use_plain && A.sched) HF_CUDA(launch_sched_update(A.sched, S.stats, st));
     if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
@@ -1052,12 +1063,12 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         b.err = errs ? errs[order[x]] : nullptr;
         const uint64_t units = (uint64_t)b.n * b.V;
         if (P.model == MODEL_DILEP) {
-            b.ept = (uint32_t)dl_ev_per_tile(b.V);
+            b.ept = (uint32_t)dl_ev_per_tile(b.V, ctx->tune[2][vclass(b.V)]);
             BL.dilep = true;
             BL.smem_dilep = std::max(BL.smem_dilep, smem_class(dl_smem_bytes((int)b.ept, (int)(b.ept * b.V))));
             units_dl += units;
         } else {
-            b.ept = (uint32_t)ev_per_tile_for(b.V);
+            b.ept = (uint32_t)ev_per_tile_for(b.V, ctx->tune[1][vclass(b.V)]);
             ++n_semi;
             BL.semi_mask = (1u << NBUCKET) - 1;
             for (int n = 0; n < NBUCKET; ++n)
@@ -1382,3 +1393,79 @@ void dispatcher_main(hf_ctx* ctx)
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ autotuner
+extern "C" hf_status hf_autotune(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_cols, uint64_t n_events,
+                                 uint32_t n_variations, uint64_t seed, int32_t* units_per_tile)
+{
+    if (!ctx || !dev_cols) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    Analysis* A = get_analysis(ctx, analysis_id);
+    if (!A) return fail(HF_ENOTFOUND, "unknown analysis id");
+    const uint32_t V = n_variations;
+    if (V < 1 || V > HF_MAX_VARIATIONS) return fail(HF_EINVAL, "n_variations must be 1..4096");
+    if (n_events == 0 || n_events > 0xFFFFFFFFull) return fail(HF_EINVAL, "sample must have 1..2^32-1 events");
+    if (hf_status s = check_cols(dev_cols, n_events, 1)) return s;
+    const bool dl = A->plan.model == MODEL_DILEP;
+    static const int cand_semi[] = {128, 256, 512, 1024};
+    static const int cand_dl[] = {32, 64, 128, 256};
+    const int* cand = dl ? cand_dl : cand_semi;
+    int& slot = ctx->tune[dl ? 2 : 1][vclass(V)];
+    const int saved = slot;
+    Cols C;
+    C.jet_off = dev_cols->jet_off;
+    C.jets = (const float4*)dev_cols->jets;
+    C.btag = dev_cols->btag;
+    C.lep = (const float4*)dev_cols->lep;
+    C.lep_q = dev_cols->lep_q;
+    C.met = (const float2*)dev_cols->met;
+    C.n_jets_total = dev_cols->n_jets_total;
+    Out O;
+    memset(&O, 0, sizeof O);
+    RunLayout RL = layout_for(n_events, V);
+    if (hf_status s = ensure_arena(ctx, RL.scratch_bytes)) return s;
+    cudaStream_t st = ctx->s_comp;
+    if (ctx->arena_free) HF_CUDA(cudaStreamWaitEvent(st, ctx->arena_free, 0));
+    cudaEvent_t e0, e1;
+    HF_CUDA(cudaEventCreate(&e0));
+    HF_CUDA(cudaEventCreate(&e1));
+    const int dflt = dl ? 128 : UNITS_PER_TILE;  // the untuned shape (one of the candidates)
+    float best_ms = 0.f, dflt_ms = 0.f;
+    int best = 0;
+    hf_status rs = HF_OK;
+    unsigned long long* prof = ctx->prof_dev;
+    ctx->prof_dev = nullptr;  // tuning runs are not profiled
+    for (int c = 0; c < 4 && rs == HF_OK; ++c) {
+        slot = cand[c];
+        float t3[3] = {0.f, 0.f, 0.f};
+        for (int rep = 0; rep < 4 && rs == HF_OK; ++rep) {  // one warm-up, then the median of three
+            cudaEventRecord(e0, st);
+            rs = enqueue_run(ctx, *A, C, n_events, V, O, ctx->arena, RL, seed, 0, false, st);
+            cudaEventRecord(e1, st);
+            if (rs == HF_OK && cudaEventSynchronize(e1) == cudaSuccess && rep > 0)
+                cudaEventElapsedTime(&t3[rep - 1], e0, e1);
+        }
+        std::sort(t3, t3 + 3);
+        const float ms = t3[1];
+        if (cand[c] == dflt) dflt_ms = ms;
+        if (rs == HF_OK && (best == 0 || ms < best_ms)) {
+            best = cand[c];
+            best_ms = ms;
+        }
+    }
+    // keep the default unless a candidate is clearly faster (timing noise)
+    if (best != dflt && dflt_ms > 0.f && best_ms > 0.97f * dflt_ms) best = dflt;
+    ctx->prof_dev = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ctx->arena_free) cudaEventCreateWithFlags(&ctx->arena_free, cudaEventDisableTiming);
+    cudaEventRecord(ctx->arena_free, st);
+    if (rs != HF_OK) {
+        slot = saved;
+        return rs;
+    }
+    slot = best;
+    if (units_per_tile) *units_per_tile = best;
+    return HF_OK;
+}

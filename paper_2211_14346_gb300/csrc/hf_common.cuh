@@ -493,9 +493,9 @@ __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsi
 __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                                           uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
                                           const uint32_t* bits, const int* uf, const float4* ureco,
-                                          unsigned long long* fc, unsigned* hist)
+                                          unsigned long long* fc, unsigned* hist, int rank, int size)
 {
-    for (int ev = threadIdx.x; ev < ne; ev += blockDim.x) {
+    for (int ev = rank; ev < ne; ev += size) {
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
         unsigned cnt = 0;
         int nflag = 0;
@@ -528,6 +528,20 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
         else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
     }
 }
+
+// ------------------------------------------------------------------ thread groups of a tile
+// A tile is processed either by the whole block or by one warp (its own
+// tile, no block-wide barrier).
+struct BlockGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
 
 // ------------------------------------------------------------------ tile shared memory
 // Shared memory of one semileptonic stage-2 tile: per event the packed Gram

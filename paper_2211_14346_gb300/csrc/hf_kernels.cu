@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
 // ------------------------------------------------------------------ host launchers
 size_t semi_tile_bytes(int n, int ept, int units) { return tile_smem_bytes(ept, units, gram_stride(n)); }
 
-int ev_per_tile_for(uint32_t V)
+int ev_per_tile_for(uint32_t V, int upt)
 {
-    int e = UNITS_PER_TILE / (int)V;
+    int e = (upt > 0 ? upt : UNITS_PER_TILE) / (int)V;
     if (e < 1) e = 1;
     if (e > MAX_EV_PER_TILE) e = MAX_EV_PER_TILE;
     return e;
@@ -149,7 +149,7 @@ typedef cudaError_t (*S2Launcher)(const Plan&, const Cols&, const Out&, const Sc
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                        uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st, cudaEvent_t* ev,
-                       const SideStreams* side)
+                       const SideStreams* side, int upt)
 {
     if (N == 0) return cudaSuccess;
     const unsigned nb = (N + 255) / 256;
@@ -166,13 +166,13 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
         k_count<<<min(nb, 4096u), 256, 0, st>>>(P, C, N, S);
         k_stage1<<<nb, 256, 0, st>>>(P, C, N, V, O, S);
         if (ev) cudaEventRecord(ev[1], st);
-        const int ept = ev_per_tile_for(V);
+        const int ept = ev_per_tile_for(V, upt);
         static const S2Launcher semi[NBUCKET] = {
             launch_s2_semi<0>, launch_s2_semi<1>, launch_s2_semi<2>,  launch_s2_semi<3>, launch_s2_semi<4>,
             launch_s2_semi<5>, launch_s2_semi<6>, launch_s2_semi<7>,  launch_s2_semi<8>, launch_s2_semi<9>,
             launch_s2_semi<10>, launch_s2_semi<11>, launch_s2_semi<12>};
         if (P.model == MODEL_DILEP) {
-            e = launch_s2_dilep(P, C, O, S, V, seed, first_id, sms, st);
+            e = launch_s2_dilep(P, C, O, S, V, seed, first_id, dl_ev_per_tile(V, upt), sms, st);
             if (e != cudaSuccess) return e;
         } else {
             // Buckets are independent: on side streams their persistent grids

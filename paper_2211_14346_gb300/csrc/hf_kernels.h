@@ -14,8 +14,9 @@ hf_status build_plan(const hf_analysis_desc* d, Plan& P);
 hf_status set_error(hf_status s, const char* msg);
 hf_status set_cuda_error(cudaError_t e, const char* what);
 
-// Events per tile of the stage-2 kernels for V variations per event.
-int ev_per_tile_for(uint32_t V);
+// Events per tile of the semileptonic stage-2 kernels for V variations per
+// event and `upt` units per tile (0 = the default, UNITS_PER_TILE).
+int ev_per_tile_for(uint32_t V, int upt = 0);
 
 // Enqueues one whole run of the path on stream st.  Scratch counters and the
 // output accumulators must be zeroed by the caller beforehand.  If ev is not
@@ -26,7 +27,7 @@ cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scr
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st);
 
 cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
-                            uint64_t first_id, int sms, cudaStream_t st);
+                            uint64_t first_id, int ept, int sms, cudaStream_t st);
 
 cudaError_t launch_plain(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                          uint64_t seed, uint64_t first_id, cudaStream_t st);
@@ -45,7 +46,7 @@ struct SideStreams {
 
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                        uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st,
-                       cudaEvent_t* ev = nullptr, const SideStreams* side = nullptr);
+                       cudaEvent_t* ev = nullptr, const SideStreams* side = nullptr, int upt = 0);
 
 // Batched runs (hf_batch.cu): the host-side shape of one batch's launches.
 struct BatchLaunch {
@@ -65,7 +66,8 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
 // Shared memory of one stage-2 tile (semileptonic multiplicity n / dilepton).
 size_t semi_tile_bytes(int n, int ept, int units);
 size_t dl_smem_bytes(int ev, int units);
-int dl_ev_per_tile(uint32_t V);
+// Events per tile of the dilepton stage-2 kernel (upt: units per tile, 0 = default).
+int dl_ev_per_tile(uint32_t V, int upt = 0);
 
 // Kernel launches of one fast-path run (count, stage 1, one per multiplicity, recheck).
 constexpr int FAST_LAUNCHES = 2 + NBUCKET + 1;

@@ -59,36 +59,21 @@ __host__ __device__ constexpr int pair_i(int p) { return p - pair_j(p) * (pair_j
 // that lanes reading the same entry of different events hit different banks.
 __host__ __device__ constexpr int gram_stride(int n) { return ntri(n) | 1; }
 
-// Top-2 tracker of candidate chi2 values with the masses of the best.
-struct Top2 {
-    float b1, b2, mt, mw;
-    __device__ __forceinline__ void add(float c, float mt_c, float mw_c)
-    {
-        const bool better = c < b1;
-        b2 = fminf(b2, fmaxf(b1, c));
-        mt = better ? mt_c : mt;
-        mw = better ? mw_c : mw;
-        b1 = fminf(b1, c);
-    }
-    __device__ __forceinline__ void merge(const Top2& o)
-    {
-        const bool better = o.b1 < b1;
-        b2 = fminf(fminf(b2, o.b2), fmaxf(b1, o.b1));
-        mt = better ? o.mt : mt;
-        mw = better ? o.mw : mw;
-        b1 = fminf(b1, o.b1);
-    }
-};
-
 // Minimum and second minimum of the triplet chi2, clamped at `cap`, with the
 // masses of the minimising candidate.  gf: packed upper triangle of the Gram
-// matrix (entry (i, j), i <= j, at tri(i, j)), s: jet scales.  Only candidates with chi2 < cap can
-// change any output (cap lies above the cut threshold by more than the error
-// bands, so a clamped minimum still decides the cut and the argmin gap
-// exactly).  Pairs and b-jets are fully unrolled for the multiplicity N: the
-// scaled Gram terms stay in registers and each candidate costs three adds,
-// one reciprocal square root, one multiply, two fused multiply-adds and the
-// top-2 update.  *cands counts the candidates evaluated.
+// matrix (entry (i, j), i <= j, at tri(i, j)), s: jet scales.  Only candidates
+// with chi2 < cap can change any output (cap lies above the cut threshold by
+// more than the error bands, so a clamped minimum still decides the cut and
+// the argmin gap exactly).  Pairs and b-jets are fully unrolled for the
+// multiplicity N, the scaled Gram terms stay in registers, and the loop runs
+// over W pairs (j, then i < j) with the b-jet k innermost.  Per W jet j the
+// terms u_k = a_k + q_jk are formed once, so a candidate costs two adds for
+// m^2 = (m^2_ij + u_k) + q_ik (a sum of non-negative terms in another order
+// than the definition's: the same relative error bound), one reciprocal
+// square root, one multiply, two fused multiply-adds, and a top-2 update that
+// keeps only the winner's m^2 (its mass is formed once at the end with the
+// same operations, hence the same value); the winner's W mass is kept per
+// pair.  *cands counts the candidates evaluated.
 template <int N>
 __device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict__ gf,
                                          const float (&s)[N > 0 ? N : 1], float cap, float& b1, float& b2,
@@ -109,30 +94,40 @@ __device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict_
             for (int i = 0; i < j; ++i) q2[i * N + j] = q2[j * N + i] = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), gf[tri(i, j)]);
         const float c_t = -P.mt * P.inv_sigma_t;
         const float c_w = -P.mW * P.inv_sigma_W;
-        Top2 ta{cap, cap, 0.0f, 0.0f};
-        unsigned nc = 0;
+        float c1 = cap, c2 = cap, bm2 = 0.0f, bmw = 0.0f;
 #pragma unroll
         for (int j = 1; j < N; ++j) {
+            float u[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) u[k] = k == j ? 0.0f : __fadd_rn(a[k], q2[j * N + k]);
 #pragma unroll
             for (int i = 0; i < j; ++i) {
-                float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2[i * N + j]);
-                float mw = __fmul_rn(pw, rsqrt_approx(pw));
-                float dw = fmaf(mw, P.inv_sigma_W, c_w);
-                float cw = __fmul_rn(dw, dw);
+                const float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2[i * N + j]);
+                const float mw = __fmul_rn(pw, rsqrt_approx(pw));
+                const float dw = fmaf(mw, P.inv_sigma_W, c_w);
+                const float cw = __fmul_rn(dw, dw);
+                const float before = c1;
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
                     if (k == i || k == j) continue;
-                    float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2[i * N + k]), q2[j * N + k]);
-                    float mt = __fmul_rn(m2, rsqrt_approx(m2));
-                    float dt = fmaf(mt, P.inv_sigma_t, c_t);
-                    float c = fmaf(dt, dt, cw);
-                    ta.add(c, mt, mw);
-                    ++nc;
+                    const float m2 = __fadd_rn(__fadd_rn(pw, u[k]), q2[i * N + k]);
+                    const float mt = __fmul_rn(m2, rsqrt_approx(m2));
+                    const float dt = fmaf(mt, P.inv_sigma_t, c_t);
+                    const float c = fmaf(dt, dt, cw);
+                    bm2 = c < c1 ? m2 : bm2;
+                    c2 = fminf(c2, fmaxf(c1, c));
+                    c1 = fminf(c1, c);
                 }
+                bmw = c1 < before ? mw : bmw;
             }
         }
-        b1 = ta.b1; b2 = ta.b2; mt_b = ta.mt; mw_b = ta.mw;
-        *cands += nc;
+        b1 = c1;
+        b2 = c2;
+        if (c1 < cap) {
+            mt_b = __fmul_rn(bm2, rsqrt_approx(bm2));
+            mw_b = bmw;
+        }
+        *cands += (unsigned)(N * (N - 1) * (N - 2) / 2);
     }
 }
 

@@ -86,7 +86,8 @@ __device__ void dilep_tile(const Plan& P, const Cols& C, const Out& O, const Scr
     }
     __syncthreads();
     // C: per-event reduction
-    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, acc.fc, acc.hist);
+    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, acc.fc, acc.hist,
+                       threadIdx.x, blockDim.x);
     __syncthreads();
 }
 
@@ -97,9 +98,9 @@ size_t dl_smem_bytes(int ev, int units)
     return (size_t)ev * (12 * 16 + 32 + 8 + 16) + (size_t)units * 20 + 64;
 }
 
-int dl_ev_per_tile(uint32_t V)
+int dl_ev_per_tile(uint32_t V, int upt)
 {
-    int e = DL_UNITS_PER_TILE / (int)V;
+    int e = (upt > 0 ? upt : DL_UNITS_PER_TILE) / (int)V;
     return e < 1 ? 1 : (e > 64 ? 64 : e);
 }
 
@@ -245,9 +246,8 @@ cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream
 }
 
 cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
-                            uint64_t first_id, int sms, cudaStream_t st)
+                            uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
-    const int ept = dl_ev_per_tile(V);
     const size_t smem = dl_smem_bytes(ept, ept * (int)V);
     static bool attr = false;
     if (!attr) {

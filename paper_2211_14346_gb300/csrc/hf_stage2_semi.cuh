@@ -21,24 +21,25 @@
 
 namespace hf {
 
-template <int N>
-__device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+template <int N, class Grp>
+__device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
                           const int* exec, int nexec, unsigned long long* fc, unsigned* hist, CutStats* st)
 {
+    const int r0 = g.rank(), gs = g.size();
     // A: stage lepton / MET, then the packed Gram matrices
-    for (int t = threadIdx.x; t < ne; t += blockDim.x) {
+    for (int t = r0; t < ne; t += gs) {
         uint2 en = ents[t];
         sm.evid[t] = en.x;
         sm.bits[t] = en.y;
         sm.lep[t] = __ldg(&C.lep[en.x]);
         sm.met[t] = __ldg(&C.met[en.x]);
     }
-    __syncthreads();
+    g.sync();
     constexpr int NT = ntri(N);
     constexpr int GST = gram_stride(N);
     if constexpr (NT > 0) {
-        for (int t = threadIdx.x; t < ne * NT; t += blockDim.x) {
+        for (int t = r0; t < ne * NT; t += gs) {
             int ev = t / NT, k = t - ev * NT;
             int j = 0;
             while ((j + 1) * (j + 2) / 2 <= k) ++j;
@@ -47,10 +48,10 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
             sm.G[ev * GST + k] = minkowski_dot2(__ldg(&C.jets[j0 + i]), __ldg(&C.jets[j0 + j]));
         }
     }
-    __syncthreads();
+    g.sync();
     // B: units
     const int nu = ne * (int)V;
-    for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+    for (int u = r0; u < nu; u += gs) {
         int ev = u / (int)V;
         uint32_t v = (uint32_t)(u - ev * (int)V);
         SemiEvent<N> se;
@@ -64,10 +65,10 @@ __device__ void semi_tile(const Plan& P, const Cols& C, const Out& O, const Scra
         sm.ureco[u] = r.reco;
         warp_tally(P, r, fc, hist, st);
     }
-    __syncthreads();
+    g.sync();
     // C: per-event reduction in variation order
-    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, fc, hist);
-    __syncthreads();
+    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, fc, hist, r0, gs);
+    g.sync();
 }
 
 // Block-level accumulators of the stage-2 kernels (shared memory).
@@ -101,6 +102,10 @@ struct S2Acc {
     }
 };
 
+// Single chunk: the block takes tiles of bucket N from its tile counter.  The
+// block-wide barriers between the phases of a tile keep the block's warps at
+// nearby code addresses of the (long, fully unrolled) unit evaluation, which
+// measured faster than independent per-warp tiles.
 template <int N>
 __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
@@ -134,8 +139,8 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Pla
         any = true;
         unsigned first = tile * (unsigned)ev_per_tile;
         int ne = (int)min((unsigned)ev_per_tile, s_fill - first);
-        semi_tile<N>(P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec, acc.fc,
-                     acc.hist, &acc.st);
+        semi_tile<N>(BlockGroup(), P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec,
+                     acc.fc, acc.hist, &acc.st);
     }
     if (!any) return;
     acc.flush(P, O, S.stats);
@@ -220,8 +225,8 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const Ba
         Scratch S = B.S;
         S.chunk = (uint32_t)c;
         TileSmem sm = carve(smem_raw, (int)ept, (int)(ept * ch.V), gram_stride(N));
-        semi_tile<N>(s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first, ne, sm,
-                     s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
+        semi_tile<N>(BlockGroup(), s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first,
+                     ne, sm, s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
     }
     if (cur >= 0) {
         const BChunk& pc = B.ch[cur];
