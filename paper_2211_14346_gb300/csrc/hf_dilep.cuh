@@ -229,6 +229,8 @@ __device__ inline DilepResD dilep_reco_d(const Plan& P, int n, unsigned btag, co
     r.m_t1 = r.m_t2 = r.m_tt = r.m_bb = 0.0;
     double best = CUDART_INF;
     unsigned bm = btag & ((1u << n) - 1u);
+    double l12[4];
+    v4_add_d(l1, l2, l12);
     for (int b1 = 0; b1 < n; ++b1) {
         if (!(bm >> b1 & 1u)) continue;
         for (int b2 = 0; b2 < n; ++b2) {
@@ -236,6 +238,16 @@ __device__ inline DilepResD dilep_reco_d(const Plan& P, int n, unsigned btag, co
             double nu1[4][4], nu2[4][4];
             const double* j1 = jet(b1);
             const double* j2 = jet(b2);
+            if (r.ok) {
+                // every solution of the pairing has m_ttbar >= m_vis (its b-jets
+                // and leptons; the neutrinos are future light-like): a pairing
+                // whose m_vis is above the best by more than FP64 rounding can
+                // neither win nor tie (ties go to the first in this order)
+                double v[4], w[4];
+                v4_add_d(j1, j2, v);
+                v4_add_d(v, l12, w);
+                if (mass_d(w) > best * (1.0 + 1.0e-12)) continue;
+            }
             int ns = dilep_pairing_d(l1, j1, l2, j2, metx, mety, P.dmW, P.dmt, nu1, nu2);
             for (int s = 0; s < ns; ++s) {
                 double t1[4], t2[4], w1[4], w2[4], tt[4];
