@@ -1,0 +1,134 @@
+"""Parity at the full sizes of the benchmark configurations, in the launch
+configuration bench.py times (autotuned tiles, device-resident columns):
+the whole chunk runs on the GPU, and contiguous blocks of events at seeded
+random offsets are compared with the FP64 oracle run on just those events
+(their global event ids, hence their smearing, unchanged): bit-exact mask and
+surviving-variation counts, reco within 1e-5.  Properties that hold at any
+size are checked on the whole chunk: cut flow starts at N V and never
+increases, its last entry equals the sum of n_surv and of the histogram, the
+mask is n_surv > 0, and the FP64 recheck stays a small fraction."""
+import functools
+
+import numpy as np
+import pytest
+
+import synth
+from synth import analyses
+from tests.parity import assert_reco
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=2)
+def _semilep_10M():
+    return synth.gen_semilep(10_000_000, 2)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2211_14346_gb300 import build, Engine
+    build.build()
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _properties(g, N, V, max_recheck_frac):
+    cf = g["cutflow"].astype(np.int64)
+    assert cf[0] == N * V
+    assert np.all(np.diff(cf) <= 0)
+    assert cf[-1] == int(g["n_surv"].astype(np.int64).sum()) == int(g["hist"].astype(np.int64).sum())
+    assert np.array_equal(g["mask"], (g["n_surv"] > 0).astype(np.uint8))
+    assert g["recheck_count"] <= max(max_recheck_frac * N * V, 50)
+
+
+def _sampled(orc, an, cols, g, *, V, seed, blocks, size, model, rng_seed):
+    rng = np.random.default_rng(rng_seed)
+    N = cols.n_events
+    for lo in rng.integers(0, N - size, blocks):
+        lo = int(lo)
+        o = orc.run(an, cols.slice(lo, lo + size), seed=seed, V=V, first_event_id=lo)
+        sl = slice(lo, lo + size)
+        assert np.array_equal(g["mask"][sl], o["mask"]), lo
+        assert np.array_equal(g["n_surv"][sl].astype(np.uint16), o["n_surv"]), lo
+        assert_reco(g["reco"][sl], o["reco"], o["reco_abs"], model=model, what="events %d.." % lo)
+
+
+def _run(eng, an, cols, *, V, seed, tune_events):
+    from paper_2211_14346_gb300 import DeviceColumns
+    aid = eng.define(an)
+    dc = DeviceColumns(cols)
+    eng.autotune(aid, dc.slice(0, min(cols.n_events, tune_events)), V=V, seed=seed)
+    g = eng.run_device(aid, dc, V=V, seed=seed).numpy()
+    assert eng.device_error() == 0
+    return g
+
+
+def test_semilep_smeared_10M_x16(eng, orc):
+    """The headline: 10,000,000 semileptonic events x 16 variations."""
+    N, V, seed = 10_000_000, 16, 1002
+    cols = _semilep_10M()
+    an = analyses.config2()
+    g = _run(eng, an, cols, V=V, seed=seed, tune_events=1_000_000)
+    _properties(g, N, V, 0.002)
+    _sampled(orc, an, cols, g, V=V, seed=seed, blocks=8, size=64, model="semilep", rng_seed=11)
+
+
+def test_semilep_unsmeared_10M(eng, orc):
+    N = 10_000_000
+    cols = _semilep_10M()
+    an = analyses.config1()
+    g = _run(eng, an, cols, V=1, seed=0, tune_events=1_000_000)
+    _properties(g, N, 1, 0.002)
+    _sampled(orc, an, cols, g, V=1, seed=0, blocks=8, size=256, model="semilep", rng_seed=12)
+
+
+def test_dilep_2M_x64(eng, orc):
+    """The ttH dilepton configuration: 2,000,000 events x 64 variations."""
+    N, V, seed = 2_000_000, 64, 1003
+    cols = synth.gen_dilep(N, 3)
+    an = analyses.config3()
+    g = _run(eng, an, cols, V=V, seed=seed, tune_events=50_000)
+    _properties(g, N, V, 0.08)
+    _sampled(orc, an, cols, g, V=V, seed=seed, blocks=4, size=24, model="dilep", rng_seed=13)
+
+
+def test_batched_workload_512_chunks(eng, orc):
+    """The batched workload of bench.py (512 chunks of 1k-100k events, both
+    models, V in {1, 8, 64}) through hf_run_batch: whole-chunk properties for
+    every chunk and oracle parity on sampled events of sampled chunks."""
+    import bench
+    from paper_2211_14346_gb300 import DeviceColumns
+    spec = bench.batched_chunks(512, 100000)
+    pool_n = max(c["n"] for c in spec)
+    pcols = {0: synth.gen_semilep(max(pool_n, 400000), 2), 1: synth.gen_dilep(max(pool_n, 200000), 3)}
+    pools = {k: DeviceColumns(v) for k, v in pcols.items()}
+    ans = {0: analyses.config2(), 1: analyses.config3()}
+    aids = {k: eng.define(v) for k, v in ans.items()}
+    seeds = {0: 1002, 1: 1003}
+    items, los = [], []
+    for c in spec:
+        pool = pools[c["model"]]
+        lo = int(c["u"] * (pool.n_events - c["n"]))
+        los.append(lo)
+        items.append(dict(aid=aids[c["model"]], cols=pool.slice(lo, lo + c["n"]), V=c["V"],
+                          seed=seeds[c["model"]], first_event_id=c["first"]))
+    res = [o.numpy() for o in eng.run_batch(items)]
+    assert eng.device_error() == 0
+    for c, g in zip(spec, res):
+        _properties(g, c["n"], c["V"], 0.08 if c["model"] == 1 else 0.002)
+    rng = np.random.default_rng(14)
+    for k in rng.choice(len(spec), 12, replace=False):
+        c, g, lo = spec[k], res[k], los[k]
+        m = c["model"]
+        size = 16 if m == 1 else 64
+        off = int(rng.integers(0, c["n"] - size))
+        sub = pcols[m].slice(lo + off, lo + off + size)
+        o = orc.run(ans[m], sub, seed=seeds[m], V=c["V"], first_event_id=c["first"] + off)
+        sl = slice(off, off + size)
+        assert np.array_equal(g["mask"][sl], o["mask"]), k
+        assert np.array_equal(g["n_surv"][sl].astype(np.uint16), o["n_surv"]), k
+        assert_reco(g["reco"][sl], o["reco"], o["reco_abs"], model="dilep" if m == 1 else "semilep",
+                    what="chunk %d" % k)
