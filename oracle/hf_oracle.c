@@ -19,7 +19,8 @@
  *     example);
  *   - semileptonic reconstruction: neutrino p_z from the W-mass constraint
  *     with the missing transverse momentum as the neutrino p_T (Sect. 6.2),
- *     and the hadronic-top jet-triplet chi-square of Eq. 1 (Sect. 6.2);
+ *     the hadronic-top jet-triplet chi-square (Eq. 1, hadronic terms) and
+ *     the full chi-square of Eq. 1 with both tops and both W bosons;
  *   - dilepton ttH reconstruction: two neutrinos from the W-mass (80.4) and
  *     top-mass (172.5) constraints with MET split between them, over all
  *     b-jet/lepton pairings, the best solution kept, the event rejected when
@@ -57,7 +58,8 @@ enum {
     ORC_HADTOP_CHI2_MAX = 6, /* best triplet chi2 < p0 (Eq. 1, hadronic part)  */
     ORC_LEP_OS = 7,          /* q1 * q2 < 0                                    */
     ORC_DILEP_SOLVABLE = 8,  /* >= 1 two-neutrino solution (Sect. 4)          */
-    ORC_HIGGS_WINDOW = 9     /* p0 < m_bb < p1 (Sect. 4, m_H = 125)           */
+    ORC_HIGGS_WINDOW = 9,    /* p0 < m_bb < p1 (Sect. 4, m_H = 125)           */
+    ORC_TTBAR_CHI2_MAX = 10  /* best full Eq. 1 chi2 < p0 (Sect. 6.2)          */
 };
 
 #define ORC_MAX_CUTS 16
@@ -215,6 +217,38 @@ int orc_w_pz(const double* lep, double metx, double mety, double mW,
     return isfinite(pz) ? 1 : 0;
 }
 
+/* Both neutrino solutions of the W-mass constraint (same mu, a, D as    */
+/* orc_w_pz).  D >= 0: the two roots (mu pz_l +- E_l sqrt(D)) / a, the  */
+/* smaller-|p_z| one first, both computed without cancellation from     */
+/* q = mu pz_l + sgn(mu pz_l) E_l sqrt(D): q / a and (E_l^2 pT^2 - mu^2)/q */
+/* (a single solution 0 when q = 0).  D < 0: the single real part        */
+/* mu pz_l / a.  a <= 0 or a non-finite value: no solution.  Returns the */
+/* number of solutions (0, 1 or 2).                                     */
+int orc_w_pz_both(const double* lep, double metx, double mety, double mW, double pz[2])
+{
+    double lx = lep[0], ly = lep[1], lz = lep[2], lE = lep[3];
+    double mu = mW * mW / 2.0 + (lx * metx + ly * mety);
+    double a = lE * lE - lz * lz;
+    double pt2 = metx * metx + mety * mety;
+    double D = mu * mu - a * pt2;
+    if (!(a > 0.0))
+        return 0;
+    if (D < 0.0) {
+        pz[0] = mu * lz / a;
+        return isfinite(pz[0]) ? 1 : 0;
+    }
+    double t = mu * lz;
+    double sq = lE * sqrt(D);
+    double q = t >= 0.0 ? t + sq : t - sq;
+    if (q == 0.0) {
+        pz[0] = 0.0;
+        return 1;
+    }
+    pz[0] = (lE * lE * pt2 - mu * mu) / q;
+    pz[1] = q / a;
+    return isfinite(pz[0]) && isfinite(pz[1]) ? 2 : 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Semileptonic: hadronic-top triplet chi-square (Eq. 1, hadronic term).*/
 /* Candidates (k, {i<j}) with k not in {i, j}: jets i, j form the W,    */
@@ -253,6 +287,79 @@ double orc_hadtop(int n, const double (*jet)[4], double mW, double mt,
                     *bj = j;
                     *mtop = m_t;
                     *mw = m_w;
+                }
+            }
+        }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Semileptonic: the full chi-square of Eq. 1 (Sect. 6.2) for ttbar ->  */
+/* (b q q')(b l nu): two top quarks and two W bosons,                   */
+/*   chi2 = ((m_kij - mt)/sigma_t)^2 + ((m_ij - mW)/sigma_W)^2           */
+/*        + ((m_l,lep,nu - mt)/sigma_t)^2 + ((m_lep,nu - mW)/sigma_W)^2,  */
+/* minimised over the hadronic b-jet k, the W jets i < j, the leptonic   */
+/* b-jet l (all distinct) and the neutrino solution r (orc_w_pz_both:    */
+/* the neutrino is (MET_x, MET_y, p_z, |p|), massless).  Enumeration: k, */
+/* then i < j as for the hadronic term, then l ascending, then r in the  */
+/* order orc_w_pz_both returns; strict minimum, ties to the first.  Fewer*/
+/* than four jets or no neutrino solution -> chi2 = +inf.  Outputs the   */
+/* hadronic and leptonic top masses and the chosen p_z.                  */
+/* ------------------------------------------------------------------ */
+double orc_ttbar(int n, const double (*jet)[4], const double* lep, double metx, double mety,
+                 double mW, double mt, double sigma_W, double sigma_t, int idx[5],
+                 double* mtop_had, double* mtop_lep, double* pz_out)
+{
+    double best = INFINITY;
+    double pz[2];
+    int nr = orc_w_pz_both(lep, metx, mety, mW, pz);
+    for (int c = 0; c < 5; ++c)
+        idx[c] = -1;
+    *mtop_had = *mtop_lep = *pz_out = 0.0;
+    if (n < 4 || nr == 0)
+        return best;
+    double W_lep[2][4], mw_lep[2];
+    for (int r = 0; r < nr; ++r) {
+        double nu[4] = {metx, mety, pz[r], sqrt(metx * metx + mety * mety + pz[r] * pz[r])};
+        v4_add(lep, nu, W_lep[r]);
+        mw_lep[r] = orc_mass(W_lep[r]);
+    }
+    for (int k = 0; k < n; ++k) {
+        for (int i = 0; i < n; ++i) {
+            if (i == k)
+                continue;
+            for (int j = i + 1; j < n; ++j) {
+                if (j == k)
+                    continue;
+                double W[4], T[4];
+                v4_add(jet[i], jet[j], W);
+                v4_add(W, jet[k], T);
+                double dt = (orc_mass(T) - mt) / sigma_t;
+                double dw = (orc_mass(W) - mW) / sigma_W;
+                double had = dt * dt + dw * dw;
+                for (int l = 0; l < n; ++l) {
+                    if (l == k || l == i || l == j)
+                        continue;
+                    for (int r = 0; r < nr; ++r) {
+                        double TL[4];
+                        v4_add(jet[l], W_lep[r], TL);
+                        double m_tl = orc_mass(TL);
+                        double dtl = (m_tl - mt) / sigma_t;
+                        double dwl = (mw_lep[r] - mW) / sigma_W;
+                        double chi2 = had + (dtl * dtl + dwl * dwl);
+                        if (chi2 < best) {
+                            best = chi2;
+                            idx[0] = k;
+                            idx[1] = i;
+                            idx[2] = j;
+                            idx[3] = l;
+                            idx[4] = r;
+                            *mtop_had = orc_mass(T);
+                            *mtop_lep = m_tl;
+                            *pz_out = pz[r];
+                        }
+                    }
                 }
             }
         }
@@ -481,6 +588,8 @@ typedef struct {
     double pz;
     int t_done, k, i, j;
     double chi2, mtop, mw;
+    int f_done, fidx[5];
+    double fchi2, fmtop_had, fmtop_lep, fpz;
     /* dilepton */
     int d_done, d_ok, pb1, pb2;
     double m_t1, m_t2, m_tt;
@@ -529,6 +638,16 @@ static void need_top(const orc_analysis* an, const orc_event* ev, orc_unit_state
     st->chi2 = orc_hadtop(ev->n, (const double(*)[4])st->jet, an->mW, an->mt,
                           an->sigma_W, an->sigma_t, &st->k, &st->i, &st->j,
                           &st->mtop, &st->mw);
+}
+
+static void need_full(const orc_analysis* an, const orc_event* ev, orc_unit_state* st)
+{
+    if (st->f_done)
+        return;
+    st->f_done = 1;
+    st->fchi2 = orc_ttbar(ev->n, (const double(*)[4])st->jet, ev->lep[0], st->metx, st->mety, an->mW,
+                          an->mt, an->sigma_W, an->sigma_t, st->fidx, &st->fmtop_had, &st->fmtop_lep,
+                          &st->fpz);
 }
 
 /* Best two-neutrino solution over ordered b-jet pairings (b1 with lepton 1,
@@ -644,6 +763,9 @@ static int cut_pass(const orc_analysis* an, int c, const orc_event* ev, orc_unit
     case ORC_HIGGS_WINDOW:
         need_higgs(an, ev, st);
         return st->h_ok && st->m_bb > p0 && st->m_bb < p1;
+    case ORC_TTBAR_CHI2_MAX:
+        need_full(an, ev, st);
+        return st->fchi2 < p0;
     default:
         return 0;
     }
@@ -696,7 +818,8 @@ static void load_event(const orc_analysis* an, uint64_t e, const uint32_t* jet_o
 typedef struct {
     int32_t passed;
     int32_t idx[4];   /* semilep: k, i, j, dneg; dilep: b1, b2, h1, h2 */
-    double q[6];      /* semilep: mtop, mW, pz, MET', chi2, -;  dilep: m_bb, m_t, m_tbar, m_tt, -, - */
+    double q[6];      /* semilep: mtop, mW, pz, MET', chi2, -; with the full fit: mtop_had, mtop_lep,
+                         pz, MET', chi2, neutrino solution;  dilep: m_bb, m_t, m_tbar, m_tt, -, - */
 } orc_unit_result;
 
 static int eval_unit(const orc_analysis* an, const orc_event* ev, uint64_t seed,
@@ -713,7 +836,22 @@ static int eval_unit(const orc_analysis* an, const orc_event* ev, uint64_t seed,
     if (res) {
         memset(res, 0, sizeof *res);
         res->passed = passed;
-        if (an->model == ORC_SEMILEP) {
+        int full = 0;
+        for (int c = 0; c < an->n_cuts; ++c)
+            full |= an->kind[c] == ORC_TTBAR_CHI2_MAX;
+        if (an->model == ORC_SEMILEP && full) {
+            /* with the full fit: (m_top hadronic, m_top leptonic, p_z of
+             * the chosen neutrino, |MET'|), histogram of the hadronic top */
+            need_full(an, ev, &st);
+            for (int c = 0; c < 4; ++c)
+                res->idx[c] = st.fidx[c];
+            res->q[0] = st.fmtop_had;
+            res->q[1] = st.fmtop_lep;
+            res->q[2] = st.fpz;
+            res->q[3] = sqrt(st.metx * st.metx + st.mety * st.mety);
+            res->q[4] = st.fchi2;
+            res->q[5] = st.fidx[4];
+        } else if (an->model == ORC_SEMILEP) {
             need_w(an, ev, &st);
             need_top(an, ev, &st);
             res->idx[0] = st.k;

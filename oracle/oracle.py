@@ -22,7 +22,7 @@ _lib = None
 MAX_CUTS = 16
 _KIND = {"njets_min": 1, "nbtag_min": 2, "lep_pt_min": 3, "met_min": 4,
          "wnu_solvable": 5, "hadtop_chi2_max": 6, "lep_os": 7,
-         "dilep_solvable": 8, "higgs_window": 9}
+         "dilep_solvable": 8, "higgs_window": 9, "ttbar_chi2_max": 10}
 _MODEL = {"semilep": 1, "dilep": 2}
 
 
@@ -73,6 +73,11 @@ def load():
         lib.orc_hadtop.argtypes = [C.c_int, vp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, vp, vp, vp, vp, vp]
         lib.orc_hadtop.restype = C.c_double
+        lib.orc_w_pz_both.argtypes = [vp, C.c_double, C.c_double, C.c_double, vp]
+        lib.orc_w_pz_both.restype = C.c_int
+        lib.orc_ttbar.argtypes = [C.c_int, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, C.c_double, vp, vp, vp, vp]
+        lib.orc_ttbar.restype = C.c_double
         lib.orc_real_roots.argtypes = [vp, C.c_int, vp]
         lib.orc_real_roots.restype = C.c_int
         lib.orc_dilep_pairing.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double,
@@ -198,6 +203,27 @@ def hadtop(jets, mW, mt, sigma_W, sigma_t):
     chi2 = lib.orc_hadtop(j.shape[0], _ptr(j), mW, mt, sigma_W, sigma_t, C.byref(k),
                           C.byref(i), C.byref(jj), C.byref(mtop), C.byref(mw))
     return dict(chi2=chi2, k=k.value, i=i.value, j=jj.value, mtop=mtop.value, mw=mw.value)
+
+
+def w_pz_both(lep, metx, mety, mW):
+    """Neutrino p_z solutions of the W-mass constraint (0, 1 or 2 values)."""
+    lib = load()
+    l4 = np.ascontiguousarray(lep, dtype=np.float64)
+    pz = np.zeros(2, np.float64)
+    n = lib.orc_w_pz_both(_ptr(l4), metx, mety, mW, _ptr(pz))
+    return pz[:n].copy()
+
+
+def ttbar(jets, lep, metx, mety, mW, mt, sigma_W, sigma_t):
+    """Full Eq. 1 fit: dict(chi2, idx (k, i, j, l, r), mtop_had, mtop_lep, pz)."""
+    lib = load()
+    j = np.ascontiguousarray(jets, dtype=np.float64).reshape(-1, 4)
+    l4 = np.ascontiguousarray(lep, dtype=np.float64)
+    idx = np.zeros(5, np.int32)
+    mh, ml, pz = C.c_double(), C.c_double(), C.c_double()
+    chi2 = lib.orc_ttbar(j.shape[0], _ptr(j), _ptr(l4), metx, mety, mW, mt, sigma_W, sigma_t, _ptr(idx),
+                         C.byref(mh), C.byref(ml), C.byref(pz))
+    return dict(chi2=chi2, idx=idx.tolist(), mtop_had=mh.value, mtop_lep=ml.value, pz=pz.value)
 
 
 def real_roots(coeffs):

@@ -15,14 +15,14 @@ carries FP32 parameters.
 
 Cut names: njets_min k | nbtag_min k | lep_pt_min x | met_min x |
 wnu_solvable | hadtop_chi2_max x | lep_os | dilep_solvable |
-higgs_window lo hi.
+higgs_window lo hi | ttbar_chi2_max x (the full Eq. 1 fit).
 """
 from __future__ import annotations
 
 import copy
 
 CUT_NAMES = ("njets_min", "nbtag_min", "lep_pt_min", "met_min", "wnu_solvable",
-             "hadtop_chi2_max", "lep_os", "dilep_solvable", "higgs_window")
+             "hadtop_chi2_max", "lep_os", "dilep_solvable", "higgs_window", "ttbar_chi2_max")
 
 
 def semilep(sigma_jet=0.0, sigma_met=0.0, sigma_t=15.0, sigma_W=10.0,
@@ -33,6 +33,20 @@ def semilep(sigma_jet=0.0, sigma_met=0.0, sigma_t=15.0, sigma_W=10.0,
     if cuts is None:
         cuts = [("njets_min", 4), ("nbtag_min", 1), ("lep_pt_min", 30.0),
                 ("met_min", 20.0), ("wnu_solvable",), ("hadtop_chi2_max", 10.0)]
+    return dict(model="semilep", cuts=list(cuts), mW=80.4, mt=172.5,
+                sigma_t=sigma_t, sigma_W=sigma_W, mH=125.0,
+                sigma_jet=sigma_jet, sigma_met=sigma_met, hist=(50, 0.0, 500.0))
+
+
+def semilep_full(sigma_jet=0.0, sigma_met=0.0, sigma_t=11.5, sigma_W=7.5, cuts=None):
+    """Semileptonic chain with the full Eq. 1 fit (both tops, both W bosons,
+    both neutrino solutions) in place of the hadronic-top cut: >= 4 jets,
+    >= 1 b-tag, lepton pT > 30, MET > 20, solvable W-mass neutrino p_z,
+    full chi2 < 20; the paper's widths 11.5 / 7.5; m_top (hadronic)
+    histogram 50 bins 0-500."""
+    if cuts is None:
+        cuts = [("njets_min", 4), ("nbtag_min", 1), ("lep_pt_min", 30.0),
+                ("met_min", 20.0), ("wnu_solvable",), ("ttbar_chi2_max", 20.0)]
     return dict(model="semilep", cuts=list(cuts), mW=80.4, mt=172.5,
                 sigma_t=sigma_t, sigma_W=sigma_W, mH=125.0,
                 sigma_jet=sigma_jet, sigma_met=sigma_met, hist=(50, 0.0, 500.0))

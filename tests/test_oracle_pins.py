@@ -276,6 +276,119 @@ def test_hadtop_too_few_jets_is_infinite(orc):
     assert orc.hadtop(jets, 80.4, 172.5, 10.0, 15.0)["chi2"] == np.inf
 
 
+# ---------------------------------------------------------------- full Eq. 1 fit
+def _nu_solutions_numpy(lep, metx, mety, mW):
+    """Neutrino p_z of the W-mass constraint by numpy.roots (an independent
+    route): real roots ordered by |p_z|, or the real part of a complex pair."""
+    mu = mW ** 2 / 2 + lep[0] * metx + lep[1] * mety
+    a = lep[3] ** 2 - lep[2] ** 2
+    roots = np.roots([a, -2 * mu * lep[2], lep[3] ** 2 * (metx ** 2 + mety ** 2) - mu ** 2])
+    if np.any(np.abs(roots.imag) > 0):
+        return [roots[0].real]
+    return sorted(roots.real.tolist(), key=abs)
+
+
+def test_w_pz_both_roots(orc):
+    """Both solutions: the numpy.roots roots in |p_z| order, each meeting the
+    W-mass constraint; the first is orc.w_pz's; D < 0 gives its real part."""
+    rng = np.random.default_rng(21)
+    n2 = n1 = 0
+    for _ in range(300):
+        lep = K.p4(*rng.uniform(-90, 90, 3), 0.0)
+        metx, mety = rng.uniform(-200, 200, 2)
+        sol = orc.w_pz_both(lep, metx, mety, 80.4)
+        ref = _nu_solutions_numpy(lep, metx, mety, 80.4)
+        ok, pz1, dneg = orc.w_pz(lep, metx, mety, 80.4)
+        assert len(sol) == len(ref)
+        assert sol[0] == pz1
+        for a, b in zip(sol, ref):
+            assert a == pytest.approx(b, rel=1e-8, abs=1e-8)
+        if len(sol) == 2:
+            n2 += 1
+            for r in sol:
+                assert K.minkowski_m2(lep + K.p4(metx, mety, r, 0.0)) == pytest.approx(80.4 ** 2, rel=1e-9)
+        else:
+            n1 += 1
+    assert n2 > 50 and n1 > 20
+
+
+def _full_chi2_bruteforce(jets, lep, metx, mety, mW, mt, sW, sT):
+    """Every (hadronic b, W pair, leptonic b, neutrino solution) by
+    itertools.permutations of four jets, masses from the Minkowski Gram sum
+    (independent of the oracle's four-vector sums); returns (chi2, key) of the
+    minimum with the oracle's enumeration order as key for ties."""
+    nus = _nu_solutions_numpy(lep, metx, mety, mW)
+
+    def m_of(vs):
+        G = 0.0
+        for va in vs:
+            for vb in vs:
+                G += va[3] * vb[3] - va[:3] @ vb[:3]
+        return np.sqrt(G) if G >= 0 else -np.sqrt(-G)
+    best, key = np.inf, None
+    seen = set()
+    for k, i, j, l in itertools.permutations(range(len(jets)), 4):
+        if i > j or (k, i, j, l) in seen:
+            continue
+        seen.add((k, i, j, l))
+        had = ((m_of([jets[i], jets[j], jets[k]]) - mt) / sT) ** 2 + ((m_of([jets[i], jets[j]]) - mW) / sW) ** 2
+        for r, pz in enumerate(nus):
+            nu = K.p4(metx, mety, pz, 0.0)
+            c = had + ((m_of([jets[l], lep, nu]) - mt) / sT) ** 2 + ((m_of([lep, nu]) - mW) / sW) ** 2
+            kk = (k, i, j, l, r)
+            if key is None or c < best - 1e-9 * max(1.0, best) or (abs(c - best) <= 1e-9 * max(1.0, best) and kk < key):
+                best, key = c, kk
+    return best, key
+
+
+def test_ttbar_full_fit_brute_force(orc):
+    """n = 4..6 jets: the oracle's minimum of the full Eq. 1 chi2 and its
+    assignment equal the brute-force enumeration's."""
+    rng = np.random.default_rng(22)
+    for n in (4, 5, 6):
+        for _ in range(12):
+            jets = [K.random_parent(5.0, rng, pmax=120) for _ in range(n)]
+            lep = K.p4(*rng.uniform(-60, 60, 3), 0.0)
+            metx, mety = rng.uniform(-80, 80, 2)
+            best, key = _full_chi2_bruteforce(jets, lep, metx, mety, 80.4, 172.5, 7.5, 11.5)
+            r = orc.ttbar(np.array(jets), lep, metx, mety, 80.4, 172.5, 7.5, 11.5)
+            assert r["chi2"] == pytest.approx(best, rel=1e-8, abs=1e-10)
+            assert tuple(r["idx"]) == key
+
+
+def test_ttbar_full_fit_planted_truth(orc):
+    """ttbar -> (b q q')(b l nu) built by two-body decays, MET = the
+    neutrino's pT: chi2 ~ 0 at the planted assignment, with the neutrino
+    solution equal to the true p_z and both top masses 172.5."""
+    rng = np.random.default_rng(23)
+    for _ in range(40):
+        th = K.random_parent(172.5, rng, pmax=150)
+        tl = K.random_parent(172.5, rng, pmax=150)
+        bh, Wh = K.two_body(th, 5.0, 80.4, rng)
+        q1, q2 = K.two_body(Wh, 5.0, 5.0, rng)
+        bl, Wl = K.two_body(tl, 5.0, 80.4, rng)
+        lep, nu = K.two_body(Wl, 0.0, 0.0, rng)
+        extra = [K.random_parent(5.0, rng, pmax=15) for _ in range(rng.integers(0, 3))]
+        jets = [q1, bh, q2, bl] + extra
+        perm = rng.permutation(len(jets))
+        shuffled = [jets[p] for p in perm]
+        pos = {orig: new for new, orig in enumerate(perm)}
+        r = orc.ttbar(np.array(shuffled), lep, nu[0], nu[1], 80.4, 172.5, 7.5, 11.5)
+        assert r["chi2"] < 1e-9
+        k, i, j, l, sol = r["idx"]
+        assert k == pos[1] and {i, j} == {pos[0], pos[2]} and l == pos[3]
+        assert r["pz"] == pytest.approx(nu[2], rel=1e-6, abs=1e-6)
+        assert r["mtop_had"] == pytest.approx(172.5, rel=1e-10)
+        assert r["mtop_lep"] == pytest.approx(172.5, rel=1e-8)
+
+
+def test_ttbar_needs_four_jets(orc):
+    rng = np.random.default_rng(2)
+    jets = np.array([K.random_parent(5.0, rng) for _ in range(3)])
+    lep = K.p4(30.0, 10.0, 5.0, 0.0)
+    assert orc.ttbar(jets, lep, 20.0, -10.0, 80.4, 172.5, 7.5, 11.5)["chi2"] == np.inf
+
+
 # ---------------------------------------------------------------- quartic
 def test_real_roots_from_known_roots(orc):
     """Polynomials built from known real roots times an irreducible
