@@ -49,11 +49,13 @@ def _args():
     p.add_argument("--requests", type=int, default=600, help="served: number of requests per arrival rate")
     p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
     p.add_argument("--rates", default="0.5,0.9,1.2", help="served: arrival rates as fractions of measured capacity")
-    p.add_argument("--workload", default="semilep16", choices=["semilep16", "batched", "served", "dilep", "unsmeared"],
+    p.add_argument("--workload", default="semilep16",
+                   choices=["semilep16", "batched", "served", "dilep", "unsmeared", "fullfit"],
                    help="semilep16: the headline (10M semileptonic events x 16 variations); "
                         "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs; "
                         "served: open-loop requests with continuous batching; dilep: 2M ttH-like dilepton events x 64; "
-                        "unsmeared: 10M semileptonic events, no smearing (the column-scan chain)")
+                        "unsmeared: 10M semileptonic events, no smearing (the column-scan chain); "
+                        "fullfit: 2M semileptonic events x 16 with the full Eq. 1 fit")
     p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
     p.add_argument("--max-chunk", type=int, default=100000, help="batched: largest chunk (log-uniform from 1000)")
     return p.parse_args()
@@ -565,7 +567,8 @@ def run_served(a):
 def run_single_workload(a):
     """dilep: 2,000,000 ttH-like dilepton events x 64 variations (data seed 3,
     Philox seed 1003); unsmeared: 10,000,000 semileptonic events, V = 1, no
-    smearing (data seed 2).  Device-resident columns; the plain
+    smearing (data seed 2); fullfit: 2,000,000 semileptonic events x 16 with
+    the full Eq. 1 fit (both tops, both W bosons) as the last cut.  Device-resident columns; the plain
     one-thread-per-event form timed beside it on the same data."""
     import numpy as np
     import torch
@@ -577,6 +580,10 @@ def run_single_workload(a):
     if a.workload == "dilep":
         N = a.events if a.events != N_EVENTS else 2_000_000
         cols, an, Vw, seed, name = synth.gen_dilep(N, 3), analyses.config3(), 64, 1003, "dilep_tth_2M_x64"
+    elif a.workload == "fullfit":
+        N = a.events if a.events != N_EVENTS else 2_000_000
+        cols, an, Vw, seed, name = (synth.gen_semilep(N, DATA_SEED), analyses.semilep_full(0.10, 10.0), V, SMEAR_SEED,
+                                    "semilep_fulleq1_2M_x16")
     else:
         N = a.events
         cols, an, Vw, seed, name = synth.gen_semilep(N, DATA_SEED), analyses.config1(), 1, 0, "semilep_unsmeared_10M"
@@ -641,7 +648,7 @@ def main():
         run_batched(a)
     elif a.workload == "served":
         run_served(a)
-    elif a.workload in ("dilep", "unsmeared"):
+    elif a.workload in ("dilep", "unsmeared", "fullfit"):
         run_single_workload(a)
     else:
         run_ours(a)

@@ -93,7 +93,8 @@ const char* hf_last_error(hf_ctx* ctx);
 /* ------------------------------------------------------------------ */
 /* Analysis description (hf_define_cuts).                               */
 /* ------------------------------------------------------------------ */
-#define HF_MODEL_SEMILEP 1 /* one lepton; needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX */
+#define HF_MODEL_SEMILEP 1 /* one lepton; needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX
+                              or HF_CUT_TTBAR_CHI2_MAX */
 #define HF_MODEL_DILEP 2   /* two leptons; needs HF_CUT_DILEP_SOLVABLE and HF_CUT_HIGGS_WINDOW   */
 
 /* Cut kinds.  Each is a pure predicate of one unit, so any user order gives
@@ -107,6 +108,11 @@ const char* hf_last_error(hf_ctx* ctx);
 #define HF_CUT_LEP_OS 7          /* q1 * q2 < 0                                            */
 #define HF_CUT_DILEP_SOLVABLE 8  /* >= 1 two-neutrino solution over b-jet pairings (Sect. 4) */
 #define HF_CUT_HIGGS_WINDOW 9    /* params[0] < m_bb < params[1] (Sect. 4)                  */
+#define HF_CUT_TTBAR_CHI2_MAX 10 /* full Eq. 1 fit (Sect. 6.2): min over the hadronic b-jet, the W
+                                    jet pair, the leptonic b-jet and the neutrino p_z solution of
+                                    the hadronic and leptonic top and W terms < params[0]; an
+                                    analysis with it reports (m_top hadronic, m_top leptonic,
+                                    chosen p_z, |MET|) and histograms the hadronic top mass */
 
 typedef struct {
     int32_t kind;      /* HF_CUT_*                                                     */
@@ -154,7 +160,8 @@ typedef struct {
     uint64_t* hist;     /* hist_nbins+2: [0] underflow, [1..nbins] bins, [nbins+1] overflow  */
     uint16_t* n_surv;   /* N: variations of the event passing every cut                  */
     float* reco;        /* 4*N: per-event mean over passing variations, summed in variation
-                           order; semileptonic (m_top, m_W, pz_nu, |MET|), dilepton
+                           order; semileptonic (m_top, m_W, pz_nu, |MET|) -- with the full
+                           fit (m_top had, m_top lep, pz_nu, |MET|) --, dilepton
                            (m_bb, m_t, m_tbar, m_ttbar); zeros when n_surv = 0           */
     uint64_t* recheck_count; /* 1: units re-evaluated in FP64 (diagnostic)              */
 } hf_results;

@@ -32,7 +32,7 @@ HF_MODEL_SEMILEP = 1
 HF_MODEL_DILEP = 2
 
 HF_CUT = {"njets_min": 1, "nbtag_min": 2, "lep_pt_min": 3, "met_min": 4, "wnu_solvable": 5,
-          "hadtop_chi2_max": 6, "lep_os": 7, "dilep_solvable": 8, "higgs_window": 9}
+          "hadtop_chi2_max": 6, "lep_os": 7, "dilep_solvable": 8, "higgs_window": 9, "ttbar_chi2_max": 10}
 
 HF_STATE_QUEUED, HF_STATE_RUNNING, HF_STATE_DONE, HF_STATE_FAILED = 0, 1, 2, 3
 

@@ -271,7 +271,7 @@ hf_status use_device(hf_ctx* ctx)
     return HF_OK;
 }
 
-bool known_kind(int k) { return k >= CUT_NJETS_MIN && k <= CUT_HIGGS_WINDOW; }
+bool known_kind(int k) { return k >= CUT_NJETS_MIN && k <= CUT_TTBAR_CHI2_MAX; }
 
 }  // namespace
 
@@ -291,14 +291,15 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     memset(&P, 0, sizeof P);
     P.model = d->event_model;
     P.n_cuts = (int)d->n_cuts;
-    bool have_top = false, have_w = false, have_dl = false, have_h = false;
+    bool have_top = false, have_w = false, have_dl = false, have_h = false, have_full = false;
     for (int c = 0; c < P.n_cuts; ++c) {
         const hf_cut& cut = d->cuts[c];
         if (!known_kind(cut.kind)) return fail(HF_EINVAL, "unknown cut kind");
         for (int k = 0; k < 4; ++k)
             if (!std::isfinite(cut.params[k])) return fail(HF_EINVAL, "non-finite cut parameter");
         if (cut.dep_mask >> c) return fail(HF_EINVAL, "a cut may depend only on earlier user-order cuts");
-        bool semi_only = cut.kind == CUT_W_NU_SOLVABLE || cut.kind == CUT_HADTOP_CHI2_MAX;
+        bool semi_only = cut.kind == CUT_W_NU_SOLVABLE || cut.kind == CUT_HADTOP_CHI2_MAX ||
+                         cut.kind == CUT_TTBAR_CHI2_MAX;
         bool dl_only = cut.kind == CUT_LEP_OS || cut.kind == CUT_DILEP_SOLVABLE || cut.kind == CUT_HIGGS_WINDOW;
         if (semi_only && P.model != MODEL_SEMILEP) return fail(HF_EINVAL, "semileptonic cut in a dilepton analysis");
         if (dl_only && P.model != MODEL_DILEP) return fail(HF_EINVAL, "dilepton cut in a semileptonic analysis");
@@ -311,12 +312,15 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
         have_w |= cut.kind == CUT_W_NU_SOLVABLE;
         have_dl |= cut.kind == CUT_DILEP_SOLVABLE;
         have_h |= cut.kind == CUT_HIGGS_WINDOW;
+        have_full |= cut.kind == CUT_TTBAR_CHI2_MAX;
     }
     P.top_thr = 0.0f;
     for (int c = 0; c < P.n_cuts; ++c)
         if (P.kind[c] == CUT_HADTOP_CHI2_MAX) P.top_thr = std::max(P.top_thr, P.p0[c]);
-    if (P.model == MODEL_SEMILEP && !(have_top && have_w))
-        return fail(HF_EINVAL, "semileptonic analysis needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX");
+    if (P.model == MODEL_SEMILEP && !((have_top || have_full) && have_w))
+        return fail(HF_EINVAL, "semileptonic analysis needs HF_CUT_W_NU_SOLVABLE and HF_CUT_HADTOP_CHI2_MAX "
+                               "or HF_CUT_TTBAR_CHI2_MAX");
+    P.has_full = have_full ? 1 : 0;
     if (P.model == MODEL_DILEP && !(have_dl && have_h))
         return fail(HF_EINVAL, "dilepton analysis needs HF_CUT_DILEP_SOLVABLE and HF_CUT_HIGGS_WINDOW");
     P.mW = d->mW;

@@ -104,77 +104,6 @@ __device__ __forceinline__ void flush_hist(const Plan& P, const Out& O, const un
 // Full unit in FP64 with the definition's formulation (user order; stage-1
 // results are already exact and are taken from s1bits).  Returns the number
 // of leading cuts passed; reco and bin are set when all pass.
-// FP64 quantities of one unit, computed on demand: the smearing normals of a
-// Box-Muller pair, a smeared jet, the smeared MET (the definition's
-// arithmetic, so that they equal those of any FP64 evaluation).
-struct LazyUnitD {
-    const Plan* P;
-    const Cols* C;
-    uint64_t event_id, seed;
-    uint32_t v, j0;
-    int n;
-    bool smear;
-    unsigned zdone, jdone;
-    bool metdone;
-    double z[16];
-    double jet[MAX_JETS][4];
-    double metx, mety;
-
-    __device__ void init(const Plan& P_, const Cols& C_, uint32_t e, uint64_t eid, uint64_t seed_, uint32_t v_)
-    {
-        P = &P_;
-        C = &C_;
-        event_id = eid;
-        seed = seed_;
-        v = v_;
-        j0 = C_.jet_off[e];
-        n = (int)(C_.jet_off[e + 1] - j0);
-        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
-        zdone = jdone = 0;
-        metdone = false;
-    }
-    __device__ void pair(int k)  // normals z[2k], z[2k+1]
-    {
-        if (zdone >> k & 1u) return;
-        zdone |= 1u << k;
-        uint4 w = philox4x32_10(ctr_of((uint32_t)(k / 2), v, event_id), key_of(seed));
-        uint32_t w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
-        double u0 = u01d(w0), u1 = u01d(w1);
-        double r = sqrt(-2.0 * log(u0));
-        double th = (2.0 * 3.141592653589793) * u1;
-        z[2 * k] = r * cos(th);
-        z[2 * k + 1] = r * sin(th);
-    }
-    __device__ const double* j(int i)
-    {
-        if (!(jdone >> i & 1u)) {
-            jdone |= 1u << i;
-            float4 jf = C->jets[j0 + i];
-            double js[4] = {jf.x, jf.y, jf.z, jf.w};
-            if (smear) {
-                pair(i / 2);
-                double s = 1.0 + P->dsigma_jet * z[i];
-                for (int c = 0; c < 4; ++c) jet[i][c] = s * js[c];
-            } else {
-                for (int c = 0; c < 4; ++c) jet[i][c] = js[c];
-            }
-        }
-        return jet[i];
-    }
-    __device__ void met(float2 mf)
-    {
-        if (metdone) return;
-        metdone = true;
-        if (smear) {
-            pair(6);
-            metx = (double)mf.x + P->dsigma_met * z[12];
-            mety = (double)mf.y + P->dsigma_met * z[13];
-        } else {
-            metx = mf.x;
-            mety = mf.y;
-        }
-    }
-};
 
 // Exact (definition) triplet minimum of a unit with little FP64 work.  An
 // FP32 pass with the stage-2 arithmetic finds the FP32 minimum b and keeps
@@ -193,7 +122,7 @@ static __device__ __noinline__ double hadtop_screened_d(const Plan& P, LazyUnitD
     float4 jf[MAX_JETS];
     float s[MAX_JETS];
     for (int i = 0; i < n; ++i) {
-        jf[i] = U.C->jets[U.j0 + i];
+        jf[i] = U.jp[i];
         s[i] = 1.0f;
     }
     if (P.smear_jets) {
@@ -342,8 +271,17 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
     U.init(P, C, e, event_id, seed, v);
     if (P.model == MODEL_DILEP) return dilep_unit_fp64(P, C, e, U, s1bits, reco, bin);
     const float2 mf = C.met[e];
-    bool top_done = false;
+    bool top_done = false, full_done = false;
     double chi2 = 0.0, mtop = 0.0, mw = 0.0;
+    FullFitD ff;
+    double lep[4];
+    {
+        const float4 lf = C.lep[e];
+        lep[0] = lf.x;
+        lep[1] = lf.y;
+        lep[2] = lf.z;
+        lep[3] = lf.w;
+    }
     int f = P.n_cuts;
     for (int c = 0; c < P.n_cuts; ++c) {
         bool pass;
@@ -358,6 +296,13 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
                 top_done = true;
             }
             pass = chi2 < P.dp0[c];
+        } else if (P.kind[c] == CUT_TTBAR_CHI2_MAX) {
+            if (!full_done) {
+                U.met(mf);
+                ff = ttbar_full_d(P, U, lep, U.metx, U.mety, nullptr, -1);
+                full_done = true;
+            }
+            pass = ff.chi2 < P.dp0[c];
         } else {
             pass = false;
         }
@@ -366,15 +311,15 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
             break;
         }
     }
-    if (f == P.n_cuts) {
+    if (f == P.n_cuts && P.has_full) {
+        U.met(mf);
+        if (!full_done) ff = ttbar_full_d(P, U, lep, U.metx, U.mety, nullptr, -1);
+        const double met = sqrt(U.metx * U.metx + U.mety * U.mety);
+        *bin = hist_bin_d(P, ff.mtop_had);
+        *reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, (float)met);
+    } else if (f == P.n_cuts) {
         if (!top_done) chi2 = hadtop_screened_d(P, U, &mtop, &mw);
         U.met(mf);
-        double lep[4];
-        float4 lf = C.lep[e];
-        lep[0] = lf.x;
-        lep[1] = lf.y;
-        lep[2] = lf.z;
-        lep[3] = lf.w;
         double pz;
         w_pz_d(lep, U.metx, U.mety, P.dmW, &pz);
         double met = sqrt(U.metx * U.metx + U.mety * U.mety);

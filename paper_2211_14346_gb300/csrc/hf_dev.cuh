@@ -28,7 +28,8 @@ enum : int {
     CUT_HADTOP_CHI2_MAX = 6,
     CUT_LEP_OS = 7,
     CUT_DILEP_SOLVABLE = 8,
-    CUT_HIGGS_WINDOW = 9
+    CUT_HIGGS_WINDOW = 9,
+    CUT_TTBAR_CHI2_MAX = 10
 };
 enum : int { MODEL_SEMILEP = 1, MODEL_DILEP = 2 };
 
@@ -50,6 +51,7 @@ struct Plan {
     int exec2[MAX_CUTS];
     float mW, mt, sigma_t, sigma_W, inv_sigma_t, inv_sigma_W, mH;
     float top_thr;     // largest threshold of the chi2 cuts (clamp of the triplet minimum)
+    int has_full;      // the analysis has a full Eq. 1 fit cut: it supplies the reco and histogram
     float mW2half, mW2half_lo;  // mW*mW/2 (exact in FP64) as a float-float pair
     float sigma_jet, sigma_met;
     int smear_jets, smear_met;

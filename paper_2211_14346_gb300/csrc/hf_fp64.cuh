@@ -123,6 +123,33 @@ __device__ inline int w_pz_d(const double* lep, double metx, double mety, double
     return isfinite(pz) ? 1 : 0;
 }
 
+// Both neutrino solutions of the W-mass constraint (the definition): D >= 0
+// the smaller-|p_z| root first, then q / a (one solution 0 when q = 0);
+// D < 0 the single real part mu pz_l / a; none when a <= 0 or not finite.
+__device__ inline int w_pz_both_d(const double* lep, double metx, double mety, double mW, double pz[2])
+{
+    double lx = lep[0], ly = lep[1], lz = lep[2], lE = lep[3];
+    double mu = mW * mW / 2.0 + (lx * metx + ly * mety);
+    double a = lE * lE - lz * lz;
+    double pt2 = metx * metx + mety * mety;
+    double D = mu * mu - a * pt2;
+    if (!(a > 0.0)) return 0;
+    if (D < 0.0) {
+        pz[0] = mu * lz / a;
+        return isfinite(pz[0]) ? 1 : 0;
+    }
+    double t = mu * lz;
+    double sq = lE * sqrt(D);
+    double q = t >= 0.0 ? t + sq : t - sq;
+    if (q == 0.0) {
+        pz[0] = 0.0;
+        return 1;
+    }
+    pz[0] = (lE * lE * pt2 - mu * mu) / q;
+    pz[1] = q / a;
+    return isfinite(pz[0]) && isfinite(pz[1]) ? 2 : 0;
+}
+
 // Hadronic-top triplet chi-square, Eq. 1: enumeration k, then i < j, k not in
 // {i, j}; strict minimum, ties to the first; n < 3 -> +inf.
 __device__ inline double hadtop_d(const EvD& ev, const Plan& P, double* mtop, double* mw)
@@ -152,5 +179,95 @@ __device__ inline double hadtop_d(const EvD& ev, const Plan& P, double* mtop, do
         }
     return best;
 }
+
+// FP64 quantities of one unit, computed on demand: the smearing normals of a
+// Box-Muller pair, a smeared jet, the smeared MET (the definition's
+// arithmetic, so that they equal those of any FP64 evaluation).
+struct LazyUnitD {
+    const Plan* P;
+    const Cols* C;
+    uint64_t event_id, seed;
+    uint32_t v, j0;
+    int n;
+    bool smear;
+    unsigned zdone, jdone;
+    bool metdone;
+    double z[16];
+    double jet[MAX_JETS][4];
+    double metx, mety;
+
+    const float4* jp;  // the event's jets (FP32 columns)
+
+    __device__ void init(const Plan& P_, const Cols& C_, uint32_t e, uint64_t eid, uint64_t seed_, uint32_t v_)
+    {
+        P = &P_;
+        C = &C_;
+        event_id = eid;
+        seed = seed_;
+        v = v_;
+        j0 = C_.jet_off[e];
+        n = (int)(C_.jet_off[e + 1] - j0);
+        jp = C_.jets + j0;
+        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
+        zdone = jdone = 0;
+        metdone = false;
+    }
+    // Same from the event's jet row (no column set at hand).
+    __device__ void init_jets(const Plan& P_, const float4* jets, int n_, uint64_t eid, uint64_t seed_, uint32_t v_)
+    {
+        P = &P_;
+        C = nullptr;
+        event_id = eid;
+        seed = seed_;
+        v = v_;
+        j0 = 0;
+        n = n_;
+        jp = jets;
+        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
+        zdone = jdone = 0;
+        metdone = false;
+    }
+    __device__ void pair(int k)  // normals z[2k], z[2k+1]
+    {
+        if (zdone >> k & 1u) return;
+        zdone |= 1u << k;
+        uint4 w = philox4x32_10(ctr_of((uint32_t)(k / 2), v, event_id), key_of(seed));
+        uint32_t w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
+        double u0 = u01d(w0), u1 = u01d(w1);
+        double r = sqrt(-2.0 * log(u0));
+        double th = (2.0 * 3.141592653589793) * u1;
+        z[2 * k] = r * cos(th);
+        z[2 * k + 1] = r * sin(th);
+    }
+    __device__ const double* j(int i)
+    {
+        if (!(jdone >> i & 1u)) {
+            jdone |= 1u << i;
+            float4 jf = jp[i];
+            double js[4] = {jf.x, jf.y, jf.z, jf.w};
+            if (smear) {
+                pair(i / 2);
+                double s = 1.0 + P->dsigma_jet * z[i];
+                for (int c = 0; c < 4; ++c) jet[i][c] = s * js[c];
+            } else {
+                for (int c = 0; c < 4; ++c) jet[i][c] = js[c];
+            }
+        }
+        return jet[i];
+    }
+    __device__ void met(float2 mf)
+    {
+        if (metdone) return;
+        metdone = true;
+        if (smear) {
+            pair(6);
+            metx = (double)mf.x + P->dsigma_met * z[12];
+            mety = (double)mf.y + P->dsigma_met * z[13];
+        } else {
+            metx = mf.x;
+            mety = mf.y;
+        }
+    }
+};
 
 }  // namespace hf

@@ -31,6 +31,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
         for (int i = 0; i <= j; ++i) g[tri(i, j)] = minkowski_dot2(jet[i], jet[j]);
     if (NT == 0) g[0] = 0.f;
     se.g = g;
+    se.jets = C.jets + j0;
     se.lep = C.lep[e];
     se.met = C.met[e];
     se.s1bits = bits;

@@ -131,6 +131,197 @@ __device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict_
     }
 }
 
+// ------------------------------------------------------------------ full Eq. 1 fit
+// Result of the full semileptonic fit of a unit (FP64, the definition's).
+struct FullFitD {
+    double chi2, mtop_had, mtop_lep, pz;
+};
+
+// The full chi-square of Eq. 1 (Sect. 6.2): hadronic top and W from jets
+// k, {i < j}, leptonic top from jet l, the lepton and a neutrino solution r
+// (w_pz_both_d), leptonic W from the lepton and that neutrino; minimum over
+// k, i < j, l (all distinct), r in that enumeration order, strict, ties to
+// the first.  n < 4 or no neutrino solution: +inf.  lep: the lepton, metx,
+// mety: the smeared MET (FP64).  Candidates are restricted to `list`
+// (codes k | i << 4 | j << 8 | l << 12 | r << 16, in enumeration order)
+// when nlist >= 0, else all are enumerated.
+static __device__ __noinline__ FullFitD ttbar_full_d(const Plan& P, LazyUnitD& U, const double* lep, double metx,
+                                                     double mety, const int* list, int nlist)
+{
+    FullFitD f;
+    f.chi2 = CUDART_INF;
+    f.mtop_had = f.mtop_lep = f.pz = 0.0;
+    const int n = U.n;
+    double pz[2];
+    const int nr = w_pz_both_d(lep, metx, mety, P.dmW, pz);
+    if (n < 4 || nr == 0) return f;
+    double Wl[2][4], mwl[2];
+    for (int r = 0; r < nr; ++r) {
+        const double nu[4] = {metx, mety, pz[r], sqrt(metx * metx + mety * mety + pz[r] * pz[r])};
+        v4_add_d(lep, nu, Wl[r]);
+        mwl[r] = mass_d(Wl[r]);
+    }
+    auto eval = [&](int k, int i, int j, int l, int r, double had, const double* T) {
+        double TL[4];
+        v4_add_d(U.j(l), Wl[r], TL);
+        const double m_tl = mass_d(TL);
+        const double dtl = (m_tl - P.dmt) / P.dsigma_t;
+        const double dwl = (mwl[r] - P.dmW) / P.dsigma_W;
+        const double chi2 = had + (dtl * dtl + dwl * dwl);
+        if (chi2 < f.chi2) {
+            f.chi2 = chi2;
+            f.mtop_had = mass_d(T);
+            f.mtop_lep = m_tl;
+            f.pz = pz[r];
+        }
+    };
+    auto had_of = [&](int k, int i, int j, double* T) {
+        double W[4];
+        v4_add_d(U.j(i), U.j(j), W);
+        v4_add_d(W, U.j(k), T);
+        const double dt = (mass_d(T) - P.dmt) / P.dsigma_t;
+        const double dw = (mass_d(W) - P.dmW) / P.dsigma_W;
+        return dt * dt + dw * dw;
+    };
+    if (nlist >= 0) {
+        int prev = -1;
+        double had = 0.0, T[4];
+        for (int t = 0; t < nlist; ++t) {
+            const int c = list[t];
+            const int k = c & 15, i = (c >> 4) & 15, j = (c >> 8) & 15, l = (c >> 12) & 15, r = (c >> 16) & 1;
+            if (r >= nr) continue;
+            if ((c & 0xfff) != prev) {
+                prev = c & 0xfff;
+                had = had_of(k, i, j, T);
+            }
+            eval(k, i, j, l, r, had, T);
+        }
+        return f;
+    }
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) {
+            if (i == k) continue;
+            for (int j = i + 1; j < n; ++j) {
+                if (j == k) continue;
+                double T[4];
+                const double had = had_of(k, i, j, T);
+                for (int l = 0; l < n; ++l) {
+                    if (l == k || l == i || l == j) continue;
+                    for (int r = 0; r < nr; ++r) eval(k, i, j, l, r, had, T);
+                }
+            }
+        }
+    return f;
+}
+
+// The full fit of a unit with little FP64 work: an FP32 screen and the
+// definition's FP64 arithmetic on the candidates that survive it.  The
+// neutrino solutions and the leptonic terms of every (l, r) are computed in
+// FP64 from the FP64-smeared MET (exact) and the FP32 jet scales s (relative
+// error <= s_rel), so each leptonic top mass is within (s_rel + 1e-15) of the
+// definition's; the hadronic terms come from the FP32 Gram form with the
+// chi2 band.  A candidate can be the FP64 minimum only if its screened value
+// is within both bands of the screened minimum; those (at most 32, else the
+// full enumeration) are evaluated in FP64 in enumeration order.  The result
+// is the definition's, so the cut needs no band and no recheck.
+// g: the event's packed Gram matrix, s: FP32 jet scales (n entries), mf: the
+// event's unsmeared MET.
+static __device__ __noinline__ FullFitD ttbar_screened(const Plan& P, LazyUnitD& U, const float* g, const float* s,
+                                                       const double* lep, float2 mf)
+{
+    FullFitD none;
+    none.chi2 = CUDART_INF;
+    none.mtop_had = none.mtop_lep = none.pz = 0.0;
+    const int n = U.n;
+    if (n < 4) return none;
+    U.met(mf);
+    double pz[2];
+    const int nr = w_pz_both_d(lep, U.metx, U.mety, P.dmW, pz);
+    if (nr == 0) return none;
+    // leptonic terms per (l, r) and their bands
+    float L[MAX_JETS][2], Lb[MAX_JETS][2];
+    {
+        double Wl[2][4];
+        double cw[2];
+        for (int r = 0; r < nr; ++r) {
+            const double nu[4] = {U.metx, U.mety, pz[r], sqrt(U.metx * U.metx + U.mety * U.mety + pz[r] * pz[r])};
+            v4_add_d(lep, nu, Wl[r]);
+            const double dwl = (mass_d(Wl[r]) - P.dmW) / P.dsigma_W;
+            cw[r] = dwl * dwl;
+        }
+        const double rel = 2.0 * (double)P.s_rel + 1.0e-12;
+        for (int l = 0; l < n; ++l) {
+            const float4 jf = U.jp[l];
+            const double sl = (double)s[l];
+            const double jl[4] = {sl * jf.x, sl * jf.y, sl * jf.z, sl * jf.w};
+            for (int r = 0; r < 2; ++r) {
+                if (r >= nr) {
+                    L[l][r] = CUDART_INF_F;
+                    Lb[l][r] = 0.f;
+                    continue;
+                }
+                double TL[4];
+                v4_add_d(jl, Wl[r], TL);
+                const double m = mass_d(TL);
+                const double d = (m - P.dmt) / P.dsigma_t;
+                const double dd = rel * fabs(m) / P.dsigma_t;
+                L[l][r] = (float)(d * d + cw[r]);
+                Lb[l][r] = (float)(2.0 * fabs(d) * dd + dd * dd) * 1.01f + 2.4e-7f * L[l][r] + 1.0e-30f;
+            }
+        }
+    }
+    // hadronic terms in FP32 (Gram form, as in the triplet cut)
+    float a[MAX_JETS];
+    for (int i = 0; i < n; ++i) a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), g[tri(i, i)]);
+    auto q2 = [&](int x, int y) {
+        const int lo = x < y ? x : y, hi = x < y ? y : x;
+        return 2.0f * __fmul_rn(__fmul_rn(s[lo], s[hi]), g[tri(lo, hi)]);
+    };
+    const float c_t = -P.mt * P.inv_sigma_t, c_w = -P.mW * P.inv_sigma_W;
+    auto had32 = [&](int k, int i, int j) {
+        const float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q2(i, j));
+        const float mw = __fmul_rn(pw, rsqrt_approx(pw));
+        const float dw = fmaf(mw, P.inv_sigma_W, c_w);
+        const float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), q2(i, k)), q2(j, k));
+        const float mt = __fmul_rn(m2, rsqrt_approx(m2));
+        const float dt = fmaf(mt, P.inv_sigma_t, c_t);
+        return fmaf(dt, dt, __fmul_rn(dw, dw));
+    };
+    // pass 1: the screened minimum; pass 2: the candidates within the bands
+    float best = CUDART_INF_F, best_band = 0.f;
+    int list[32];
+    int nl = 0;
+    bool overflow = false;
+    for (int pass = 0; pass < 2 && !overflow; ++pass) {
+        for (int k = 0; k < n && !overflow; ++k)
+            for (int i = 0; i < n && !overflow; ++i) {
+                if (i == k) continue;
+                for (int j = i + 1; j < n && !overflow; ++j) {
+                    if (j == k) continue;
+                    const float h = had32(k, i, j);
+                    const float hb = chi2_band(P, h);
+                    for (int l = 0; l < n && !overflow; ++l) {
+                        if (l == k || l == i || l == j) continue;
+                        for (int r = 0; r < nr; ++r) {
+                            const float c = __fadd_rn(h, L[l][r]);
+                            const float cb = hb + Lb[l][r] + 2.4e-7f * c;
+                            if (pass == 0) {
+                                if (c < best) {
+                                    best = c;
+                                    best_band = cb;
+                                }
+                            } else if (c <= best + best_band + cb) {
+                                if (nl < 32) list[nl++] = k | i << 4 | j << 8 | l << 12 | r << 16;
+                                else overflow = true;
+                            }
+                        }
+                    }
+                }
+            }
+    }
+    return ttbar_full_d(P, U, lep, U.metx, U.mety, list, overflow ? -1 : nl);
+}
+
 // Cap of the clamped triplet minimum for a chi2 cut at thr: above thr by
 // 2.5 bands, so that a minimum at the cap is a certain failure and a second
 // minimum at the cap leaves a certain argmin gap.
@@ -237,11 +428,24 @@ static __device__ __noinline__ float w_pz_fp64(const Plan& P, float4 l, float2 m
 template <int N>
 struct SemiEvent {
     const float* g;  // packed Gram matrix (shared memory, or registers in the plain form)
+    const float4* jets;  // the event's jets in global memory (for the full fit in FP64)
     float4 lep;
     float2 met;
     unsigned s1bits;
     uint64_t event_id;
 };
+
+// The full Eq. 1 fit of a unit (exact: the FP32 screen and the FP64
+// definition on its survivors).
+template <int N>
+__device__ __noinline__ FullFitD semi_full_fit(const Plan& P, const SemiEvent<N>& ev, const float* s, uint32_t v,
+                                               uint64_t seed)
+{
+    LazyUnitD U;
+    U.init_jets(P, ev.jets, N, ev.event_id, seed, v);
+    const double lep[4] = {ev.lep.x, ev.lep.y, ev.lep.z, ev.lep.w};
+    return ttbar_screened(P, U, ev.g, s, lep, ev.met);
+}
 
 // Scheduler statistics of one block (shared memory).
 struct CutStats {
@@ -297,6 +501,8 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
     }
     float b1 = CUDART_INF_F, b2 = CUDART_INF_F, mt_b = 0.f, mw_b = 0.f;
     bool top_done = false;
+    FullFitD ff;
+    bool full_done = false;
     float met = 0.f, met_err = 0.f;
     bool met_done = false;
     unsigned evald = 0, passd = 0;
@@ -337,10 +543,16 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             }
             pass = b1 < P.p0[c];
             unsure = fabsf(b1 - P.p0[c]) <= chi2_band(P, b1);
+        } else if (kind == CUT_TTBAR_CHI2_MAX) {
+            if (!full_done) {
+                ff = semi_full_fit<N>(P, ev, s, v, seed);
+                full_done = true;
+            }
+            pass = ff.chi2 < P.dp0[c];  // FP64, the definition's value
         }
         const unsigned dt = (unsigned)(clock64() - t0);
-        if (kind == CUT_HADTOP_CHI2_MAX) out.cyc_top += dt;
-        else out.cyc_met += dt;
+        if (kind == CUT_MET_MIN) out.cyc_met += dt;
+        else out.cyc_top += dt;
         evald |= 1u << c;
         if (pass) passd |= 1u << c;
         out.evald = evald;
@@ -348,7 +560,16 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         if (unsure) return out;  // f = -1: FP64 recheck
         if (!pass) phase1 = false;
     }
-    if (f == P.n_cuts) {
+    if (f == P.n_cuts && P.has_full) {
+        // survivor of an analysis with the full fit: its (exact) values
+        if (!full_done) {
+            ff = semi_full_fit<N>(P, ev, s, v, seed);
+            full_done = true;
+        }
+        if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
+        out.bin = hist_bin_d(P, ff.mtop_had);
+        out.reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, met);
+    } else if (f == P.n_cuts) {
         // survivor: reconstructed quantities must be certain as well
         if (!top_done) return out;  // (the model always has the chi2 cut)
         if (b2 - b1 <= chi2_band(P, b1) + chi2_band(P, b2)) return out;  // argmin near-tie

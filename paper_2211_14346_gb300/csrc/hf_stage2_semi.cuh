@@ -56,6 +56,7 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         uint32_t v = (uint32_t)(u - ev * (int)V);
         SemiEvent<N> se;
         se.g = sm.G + ev * GST;
+        se.jets = C.jets + __ldg(&C.jet_off[sm.evid[ev]]);
         se.lep = sm.lep[ev];
         se.met = sm.met[ev];
         se.s1bits = sm.bits[ev];
