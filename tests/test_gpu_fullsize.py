@@ -132,3 +132,14 @@ def test_batched_workload_512_chunks(eng, orc):
         assert np.array_equal(g["n_surv"][sl].astype(np.uint16), o["n_surv"]), k
         assert_reco(g["reco"][sl], o["reco"], o["reco_abs"], model="dilep" if m == 1 else "semilep",
                     what="chunk %d" % k)
+
+
+def test_fullfit_2M_x16(eng, orc):
+    """The full Eq. 1 fit workload of bench.py: 2,000,000 semileptonic events
+    x 16 variations with the fit as the last cut."""
+    N, V, seed = 2_000_000, 16, 1002
+    cols = synth.gen_semilep(N, 2)
+    an = analyses.semilep_full(0.10, 10.0)
+    g = _run(eng, an, cols, V=V, seed=seed, tune_events=200_000)
+    _properties(g, N, V, 0.002)
+    _sampled(orc, an, cols, g, V=V, seed=seed, blocks=6, size=48, model="semilep", rng_seed=15)
