@@ -1003,12 +1003,15 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     // validate; semileptonic chunks first (the kernels take each model's chunks as one range)
     std::vector<uint32_t> order;
     order.reserve(n_chunks);
-    for (int pass = 0; pass < 2; ++pass)
+    uint32_t n_semi0 = 0;
+    for (int pass = 0; pass < 3; ++pass)  // triplet-only semileptonic, full-fit semileptonic, dilepton
         for (uint32_t i = 0; i < n_chunks; ++i) {
             const hf_chunk& k = chunks[i];
             Analysis* A = get_analysis(ctx, k.analysis_id);
             if (!A) return fail(HF_ENOTFOUND, "a chunk names an unknown analysis id");
-            if ((A->plan.model == MODEL_DILEP) != (pass == 1)) continue;
+            const int cls = A->plan.model == MODEL_DILEP ? 2 : (A->plan.has_full ? 1 : 0);
+            if (cls != pass) continue;
+            if (pass == 0) ++n_semi0;
             if (k.n_variations < 1 || k.n_variations > HF_MAX_VARIATIONS)
                 return fail(HF_EINVAL, "a chunk's n_variations is outside 1..4096");
             if (k.n_events > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per chunk");
@@ -1074,7 +1077,8 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         } else {
             b.ept = (uint32_t)ev_per_tile_for(b.V, ctx->tune[1][vclass(b.V)]);
             ++n_semi;
-            BL.semi_mask = (1u << NBUCKET) - 1;
+            if (P.has_full) BL.full_mask = (1u << NBUCKET) - 1;
+            else BL.semi_mask = (1u << NBUCKET) - 1;
             for (int n = 0; n < NBUCKET; ++n)
                 BL.smem_semi[n] = std::max(BL.smem_semi[n],
                                            smem_class(semi_tile_bytes(n, (int)b.ept, (int)(b.ept * b.V))));
@@ -1103,7 +1107,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     L.off_cnt = o = align_up(o, 256);
     o += 4 * 32 * (size_t)nc;
     L.off_tctr = o = align_up(o, 256);
-    o += 4 * 16;
+    o += 4 * 32;
     L.off_fb = o = align_up(o, 256);
     o += 8 * fb_words;
     L.off_bucket = o = align_up(o, 256);
@@ -1151,6 +1155,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     B.bucket = (uint2*)(dbase + L.off_bucket);
     B.n_chunks = nc;
     B.n_semi = n_semi;
+    B.n_semi0 = n_semi0;
     B.n_blocks = (uint32_t)blocks;
     B.n_plans = np;
     {
@@ -1204,7 +1209,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     // the launch sequence: replay the captured graph when it was captured for
     // the same arena, table layout, launch shape and scheduler states
     const BatchDev* Bd = (const BatchDev*)(dbase + L.off_dev);
-    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)Bd, (uint64_t)ctx->side.n, BL.semi_mask, BL.dilep,
+    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)Bd, (uint64_t)ctx->side.n, BL.semi_mask, BL.full_mask, BL.dilep,
                                  BL.smem_dilep, np};
     for (int n = 0; n < NBUCKET; ++n) key.push_back(BL.smem_semi[n]);
     for (uint32_t p = 0; p < np; ++p) {

@@ -46,7 +46,7 @@ __global__ void k_bzero(const BatchDev* __restrict__ Bp)
 {
     const BatchDev& B = *Bp;
     if (blockIdx.x == 0) {
-        if (threadIdx.x < 16) B.tctr[threadIdx.x] = 0;
+        if (threadIdx.x < 32) B.tctr[threadIdx.x] = 0;
         if (threadIdx.x < 8) {
             unsigned* w[8] = {B.S.rc_count, B.S.rc_valid, B.S.pend_count, B.S.err, nullptr, nullptr, nullptr,
                               nullptr};
@@ -224,9 +224,16 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
     k_btiles<<<NBUCKET, 1024, 0, st>>>(B);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     static const BS2Launcher semi[NBUCKET] = {
-        launch_bs2_semi<0>, launch_bs2_semi<1>, launch_bs2_semi<2>,  launch_bs2_semi<3>,  launch_bs2_semi<4>,
-        launch_bs2_semi<5>, launch_bs2_semi<6>, launch_bs2_semi<7>,  launch_bs2_semi<8>,  launch_bs2_semi<9>,
-        launch_bs2_semi<10>, launch_bs2_semi<11>, launch_bs2_semi<12>};
+        launch_bs2_semi<0, false>,  launch_bs2_semi<1, false>,  launch_bs2_semi<2, false>,
+        launch_bs2_semi<3, false>,  launch_bs2_semi<4, false>,  launch_bs2_semi<5, false>,
+        launch_bs2_semi<6, false>,  launch_bs2_semi<7, false>,  launch_bs2_semi<8, false>,
+        launch_bs2_semi<9, false>,  launch_bs2_semi<10, false>, launch_bs2_semi<11, false>,
+        launch_bs2_semi<12, false>};
+    static const BS2Launcher full[NBUCKET] = {
+        launch_bs2_semi<0, true>,  launch_bs2_semi<1, true>,  launch_bs2_semi<2, true>,  launch_bs2_semi<3, true>,
+        launch_bs2_semi<4, true>,  launch_bs2_semi<5, true>,  launch_bs2_semi<6, true>,  launch_bs2_semi<7, true>,
+        launch_bs2_semi<8, true>,  launch_bs2_semi<9, true>,  launch_bs2_semi<10, true>, launch_bs2_semi<11, true>,
+        launch_bs2_semi<12, true>};
     const bool fork = side && side->n > 0;
     if (fork) {
         if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
@@ -239,9 +246,14 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
         if ((e = launch_bs2_dilep(B, L.smem_dilep, L.sms, sn)) != cudaSuccess) return e;
     }
     for (int n = NBUCKET - 1; n >= 0; --n) {
-        if (!(L.semi_mask >> n & 1u)) continue;
-        cudaStream_t sn = fork ? side->s[x++ % side->n] : st;
-        if ((e = semi[n](B, L.smem_semi[n], L.sms, sn)) != cudaSuccess) return e;
+        if (L.full_mask >> n & 1u) {
+            cudaStream_t sn = fork ? side->s[x++ % side->n] : st;
+            if ((e = full[n](B, L.smem_semi[n], L.sms, sn)) != cudaSuccess) return e;
+        }
+        if (L.semi_mask >> n & 1u) {
+            cudaStream_t sn = fork ? side->s[x++ % side->n] : st;
+            if ((e = semi[n](B, L.smem_semi[n], L.sms, sn)) != cudaSuccess) return e;
+        }
     }
     if (fork) {
         for (int i = 0; i < side->n; ++i) {

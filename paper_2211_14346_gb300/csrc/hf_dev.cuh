@@ -147,9 +147,11 @@ struct BatchDev {
     const int* const* exec;       // [plans] stage-2 execution order of each plan (its scheduler's)
     unsigned long long* stats;    // [plans][3*MAX_CUTS] scheduler statistics of the batch
     unsigned* tpre;               // [NBUCKET][n_chunks+1] tile prefix over chunks per bucket
-    unsigned* tctr;               // [16] tile counters: semileptonic per multiplicity, [15] dilepton
+    unsigned* tctr;               // [32] tile counters: [n] semileptonic multiplicity n, [16 + n] the
+                                  // same for full-fit analyses, [15] dilepton
     uint2* bucket;                // stage-2 work of every chunk (chunk c from ev0)
     uint32_t n_chunks, n_semi;    // chunks [0, n_semi) are semileptonic
+    uint32_t n_semi0;             // of which [0, n_semi0) without and [n_semi0, n_semi) with the full fit
     uint32_t n_blocks;            // stage-1 blocks of the batch
     uint32_t n_plans;
     Scratch S;                    // recheck list, pending slots, error word of the batch

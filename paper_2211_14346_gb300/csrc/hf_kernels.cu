@@ -167,10 +167,18 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
         k_stage1<<<nb, 256, 0, st>>>(P, C, N, V, O, S);
         if (ev) cudaEventRecord(ev[1], st);
         const int ept = ev_per_tile_for(V, upt);
-        static const S2Launcher semi[NBUCKET] = {
-            launch_s2_semi<0>, launch_s2_semi<1>, launch_s2_semi<2>,  launch_s2_semi<3>, launch_s2_semi<4>,
-            launch_s2_semi<5>, launch_s2_semi<6>, launch_s2_semi<7>,  launch_s2_semi<8>, launch_s2_semi<9>,
-            launch_s2_semi<10>, launch_s2_semi<11>, launch_s2_semi<12>};
+        static const S2Launcher semi_t[NBUCKET] = {
+            launch_s2_semi<0, false>,  launch_s2_semi<1, false>,  launch_s2_semi<2, false>,
+            launch_s2_semi<3, false>,  launch_s2_semi<4, false>,  launch_s2_semi<5, false>,
+            launch_s2_semi<6, false>,  launch_s2_semi<7, false>,  launch_s2_semi<8, false>,
+            launch_s2_semi<9, false>,  launch_s2_semi<10, false>, launch_s2_semi<11, false>,
+            launch_s2_semi<12, false>};
+        static const S2Launcher semi_f[NBUCKET] = {
+            launch_s2_semi<0, true>,  launch_s2_semi<1, true>,  launch_s2_semi<2, true>,  launch_s2_semi<3, true>,
+            launch_s2_semi<4, true>,  launch_s2_semi<5, true>,  launch_s2_semi<6, true>,  launch_s2_semi<7, true>,
+            launch_s2_semi<8, true>,  launch_s2_semi<9, true>,  launch_s2_semi<10, true>, launch_s2_semi<11, true>,
+            launch_s2_semi<12, true>};
+        const S2Launcher* semi = P.has_full ? semi_f : semi_t;
         if (P.model == MODEL_DILEP) {
             e = launch_s2_dilep(P, C, O, S, V, seed, first_id, dl_ev_per_tile(V, upt), sms, st);
             if (e != cudaSuccess) return e;

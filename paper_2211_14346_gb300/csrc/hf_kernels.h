@@ -22,7 +22,7 @@ int ev_per_tile_for(uint32_t V, int upt = 0);
 // output accumulators must be zeroed by the caller beforehand.  If ev is not
 // null, ev[0..3] are recorded before stage 1, before stage 2, before the
 // recheck and at the end.
-template <int N>
+template <int N, bool F>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st);
 
@@ -51,13 +51,14 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
 // Batched runs (hf_batch.cu): the host-side shape of one batch's launches.
 struct BatchLaunch {
     int sms;
-    unsigned semi_mask;            // bit n: some semileptonic chunk has events with n jets
-    size_t smem_semi[NBUCKET];     // dynamic shared memory of the multiplicity-n kernel
+    unsigned semi_mask;            // bit n: launch the multiplicity-n kernel (triplet-only analyses)
+    unsigned full_mask;            // the same for analyses with the full Eq. 1 fit
+    size_t smem_semi[NBUCKET];     // dynamic shared memory of the multiplicity-n kernels
     bool dilep;                    // the batch has dilepton chunks
     size_t smem_dilep;
 };
 typedef cudaError_t (*BS2Launcher)(const BatchDev*, size_t, int, cudaStream_t);
-template <int N>
+template <int N, bool F>
 cudaError_t launch_bs2_semi(const BatchDev* B, size_t smem, int sms, cudaStream_t st);
 cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream_t st);
 // Enqueues the whole batch (B in device memory) on st; stage-2 kernels overlap

@@ -13,7 +13,7 @@ namespace hf {
 // ------------------------------------------------------------------ plain form
 // One thread per event, all cuts in user order, jets read from global memory
 // into registers, no compaction, no staging, no reordering.
-template <int N>
+template <int N, bool F>
 __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t e,
                                  uint32_t V, uint64_t seed, uint64_t first_id, unsigned bits,
                                  unsigned long long* fc, unsigned* hist)
@@ -41,7 +41,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
     int nflag = 0;
     uint16_t vs[64];
     for (uint32_t v = 0; v < V; ++v) {
-        UnitOut r = semi_unit_f<N>(P, P.exec2, P.n_exec2, se, v, seed);
+        UnitOut r = semi_unit_f<N, F>(P, P.exec2, P.n_exec2, se, v, seed);
         if (r.f < 0) {
             if (nflag < 64) {
                 vs[nflag++] = (uint16_t)v;
@@ -65,15 +65,15 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
     else pend_event(P, C, O, S, e, first_id + e, seed, bits, cnt, sum, comp, vs, nflag, fc, hist);
 }
 
-template <int N>
+template <int N, bool F>
 __device__ __forceinline__ void plain_dispatch(int n, const Plan& P, const Cols& C, const Out& O, const Scratch& S,
                                                uint32_t e, uint32_t V, uint64_t seed, uint64_t first_id,
                                                unsigned bits, unsigned long long* fc, unsigned* hist)
 {
     if (n == N) {
-        plain_semi_event<N>(P, C, O, S, e, V, seed, first_id, bits, fc, hist);
+        plain_semi_event<N, F>(P, C, O, S, e, V, seed, first_id, bits, fc, hist);
     }
-    if constexpr (N > 0) plain_dispatch<N - 1>(n, P, C, O, S, e, V, seed, first_id, bits, fc, hist);
+    if constexpr (N > 0) plain_dispatch<N - 1, F>(n, P, C, O, S, e, V, seed, first_id, bits, fc, hist);
 }
 
 // Semileptonic model (the dilepton plain kernel is in hf_plain_dilep.cu).
@@ -99,7 +99,10 @@ __global__ void __launch_bounds__(BLOCK) k_plain(const Plan P, const Cols C, uin
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
                 write_zero_event(O, e);
             } else {
-                plain_dispatch<MAX_JETS>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);
+                if (P.has_full)
+                    plain_dispatch<MAX_JETS, true>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);
+                else
+                    plain_dispatch<MAX_JETS, false>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);
             }
         }
     }

@@ -1,15 +1,15 @@
 // hf_s2_semi_b.cu -- instantiations of the semileptonic stage-2 kernels (single
-// chunk and batched) for jet multiplicities 8, 9, 10.
+// chunk and batched, triplet-only analyses) for jet multiplicities 8, 9, 10.
 #include "hf_stage2_semi.cuh"
 
 namespace hf {
-template cudaError_t launch_s2_semi<8>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                       uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_bs2_semi<8>(const BatchDev*, size_t, int, cudaStream_t);
-template cudaError_t launch_s2_semi<9>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                       uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_bs2_semi<9>(const BatchDev*, size_t, int, cudaStream_t);
-template cudaError_t launch_s2_semi<10>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                       uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_bs2_semi<10>(const BatchDev*, size_t, int, cudaStream_t);
+template cudaError_t launch_s2_semi<8, false>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<8, false>(const BatchDev*, size_t, int, cudaStream_t);
+template cudaError_t launch_s2_semi<9, false>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<9, false>(const BatchDev*, size_t, int, cudaStream_t);
+template cudaError_t launch_s2_semi<10, false>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<10, false>(const BatchDev*, size_t, int, cudaStream_t);
 }  // namespace hf

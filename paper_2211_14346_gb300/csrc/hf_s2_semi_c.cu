@@ -1,12 +1,12 @@
 // hf_s2_semi_c.cu -- instantiations of the semileptonic stage-2 kernels (single
-// chunk and batched) for jet multiplicities 11, 12.
+// chunk and batched, triplet-only analyses) for jet multiplicities 11, 12.
 #include "hf_stage2_semi.cuh"
 
 namespace hf {
-template cudaError_t launch_s2_semi<11>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                       uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_bs2_semi<11>(const BatchDev*, size_t, int, cudaStream_t);
-template cudaError_t launch_s2_semi<12>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
-                                       uint64_t, uint64_t, int, int, cudaStream_t);
-template cudaError_t launch_bs2_semi<12>(const BatchDev*, size_t, int, cudaStream_t);
+template cudaError_t launch_s2_semi<11, false>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<11, false>(const BatchDev*, size_t, int, cudaStream_t);
+template cudaError_t launch_s2_semi<12, false>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<12, false>(const BatchDev*, size_t, int, cudaStream_t);
 }  // namespace hf

@@ -1,0 +1,9 @@
+// hf_s2_semi_g.cu -- instantiations of the semileptonic stage-2 kernels (single
+// chunk and batched, with the full Eq. 1 fit) for jet multiplicities 10.
+#include "hf_stage2_semi.cuh"
+
+namespace hf {
+template cudaError_t launch_s2_semi<10, true>(const Plan&, const Cols&, const Out&, const Scratch&, uint32_t,
+                                           uint64_t, uint64_t, int, int, cudaStream_t);
+template cudaError_t launch_bs2_semi<10, true>(const BatchDev*, size_t, int, cudaStream_t);
+}  // namespace hf

@@ -460,7 +460,9 @@ struct CutStats {
 // precede the earliest known failure in USER order and were not evaluated are
 // evaluated in user order, so that the reported number of leading cuts passed
 // is the user-order one whatever the execution order.
-template <int N>
+// F: the analysis has the full Eq. 1 fit (instantiated separately, so that the
+// triplet-only chain carries none of its code or registers).
+template <int N, bool F>
 __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const SemiEvent<N>& ev,
                                uint32_t v, uint64_t seed)
 {
@@ -544,11 +546,13 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             pass = b1 < P.p0[c];
             unsure = fabsf(b1 - P.p0[c]) <= chi2_band(P, b1);
         } else if (kind == CUT_TTBAR_CHI2_MAX) {
-            if (!full_done) {
-                ff = semi_full_fit<N>(P, ev, s, v, seed);
-                full_done = true;
+            if constexpr (F) {
+                if (!full_done) {
+                    ff = semi_full_fit<N>(P, ev, s, v, seed);
+                    full_done = true;
+                }
+                pass = ff.chi2 < P.dp0[c];  // FP64, the definition's value
             }
-            pass = ff.chi2 < P.dp0[c];  // FP64, the definition's value
         }
         const unsigned dt = (unsigned)(clock64() - t0);
         if (kind == CUT_MET_MIN) out.cyc_met += dt;
@@ -560,15 +564,17 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         if (unsure) return out;  // f = -1: FP64 recheck
         if (!pass) phase1 = false;
     }
-    if (f == P.n_cuts && P.has_full) {
-        // survivor of an analysis with the full fit: its (exact) values
-        if (!full_done) {
-            ff = semi_full_fit<N>(P, ev, s, v, seed);
-            full_done = true;
+    if constexpr (F) {
+        if (f == P.n_cuts) {
+            // survivor of an analysis with the full fit: its (exact) values
+            if (!full_done) {
+                ff = semi_full_fit<N>(P, ev, s, v, seed);
+                full_done = true;
+            }
+            if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
+            out.bin = hist_bin_d(P, ff.mtop_had);
+            out.reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, met);
         }
-        if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
-        out.bin = hist_bin_d(P, ff.mtop_had);
-        out.reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, met);
     } else if (f == P.n_cuts) {
         // survivor: reconstructed quantities must be certain as well
         if (!top_done) return out;  // (the model always has the chi2 cut)

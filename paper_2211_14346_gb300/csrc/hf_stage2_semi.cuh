@@ -21,7 +21,7 @@
 
 namespace hf {
 
-template <int N, class Grp>
+template <int N, bool F, class Grp>
 __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
                           const int* exec, int nexec, unsigned long long* fc, unsigned* hist, CutStats* st)
@@ -56,12 +56,12 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         uint32_t v = (uint32_t)(u - ev * (int)V);
         SemiEvent<N> se;
         se.g = sm.G + ev * GST;
-        se.jets = C.jets + __ldg(&C.jet_off[sm.evid[ev]]);
+        se.jets = F ? C.jets + __ldg(&C.jet_off[sm.evid[ev]]) : nullptr;
         se.lep = sm.lep[ev];
         se.met = sm.met[ev];
         se.s1bits = sm.bits[ev];
         se.event_id = first_id + sm.evid[ev];
-        UnitOut r = semi_unit_f<N>(P, exec, nexec, se, v, seed);
+        UnitOut r = semi_unit_f<N, F>(P, exec, nexec, se, v, seed);
         sm.uf[u] = r.f;
         sm.ureco[u] = r.reco;
         warp_tally(P, r, fc, hist, st);
@@ -107,7 +107,7 @@ struct S2Acc {
 // block-wide barriers between the phases of a tile keep the block's warps at
 // nearby code addresses of the (long, fully unrolled) unit evaluation, which
 // measured faster than independent per-warp tiles.
-template <int N>
+template <int N, bool F>
 __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
                                                        int ev_per_tile)
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Pla
         any = true;
         unsigned first = tile * (unsigned)ev_per_tile;
         int ne = (int)min((unsigned)ev_per_tile, s_fill - first);
-        semi_tile<N>(BlockGroup(), P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec,
+        semi_tile<N, F>(BlockGroup(), P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec,
                      acc.fc, acc.hist, &acc.st);
     }
     if (!any) return;
@@ -174,7 +174,10 @@ __device__ __forceinline__ void load_plan(Plan* dst, const Plan* src)
     for (int i = threadIdx.x; i < (int)(sizeof(Plan) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-template <int N>
+// F = false: the chunks [0, n_semi0) (triplet-only analyses); F = true: the
+// chunks [n_semi0, n_semi) (analyses with the full fit), each with its own
+// tile counter.
+template <int N, bool F>
 __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const BatchDev* __restrict__ Bp)
 {
     extern __shared__ __align__(16) char smem_raw[];
@@ -184,17 +187,19 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const Ba
     __shared__ int s_nexec;
     __shared__ unsigned s_tile, s_chunk;
     const BatchDev& B = *Bp;
-    const unsigned nc = B.n_chunks, ns = B.n_semi;
+    const unsigned nc = B.n_chunks;
+    const unsigned c0 = F ? B.n_semi0 : 0u, c1 = F ? B.n_semi : B.n_semi0;
+    if (c0 == c1) return;
     const unsigned* pre = B.tpre + (size_t)N * (nc + 1);
-    const unsigned total = pre[ns];
+    const unsigned t0 = pre[c0], total = pre[c1] - t0;
     if (total == 0) return;
     acc.zero();
     int cur = -1;
     while (true) {
         if (threadIdx.x == 0) {
-            unsigned t = atomicAdd(&B.tctr[N], 1u);
+            unsigned t = atomicAdd(&B.tctr[N + (F ? 16 : 0)], 1u);
             s_tile = t;
-            if (t < total) s_chunk = upper_chunk(pre, 0, ns, t);
+            if (t < total) s_chunk = upper_chunk(pre, c0, c1, t + t0);
         }
         __syncthreads();
         const unsigned t = s_tile;
@@ -221,12 +226,12 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const Ba
         unsigned base = 0;
         for (int b = 0; b < N; ++b) base += ch.cnt[b];
         const unsigned fill = ch.cnt[16 + N];
-        const unsigned first = (t - pre[c]) * ept;
+        const unsigned first = (t + t0 - pre[c]) * ept;
         const int ne = (int)min(ept, fill - first);
         Scratch S = B.S;
         S.chunk = (uint32_t)c;
         TileSmem sm = carve(smem_raw, (int)ept, (int)(ept * ch.V), gram_stride(N));
-        semi_tile<N>(BlockGroup(), s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first,
+        semi_tile<N, F>(BlockGroup(), s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first,
                      ne, sm, s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
     }
     if (cur >= 0) {
@@ -236,36 +241,36 @@ __global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const Ba
 }
 
 // Launches the kernel of multiplicity N as a persistent grid (one wave).
-template <int N>
+template <int N, bool F>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
     size_t smem = tile_smem_bytes(ept, ept * (int)V, gram_stride(N));
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_stage2_semi<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_stage2_semi<N, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr = true;
     }
     int bs = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_semi<N>, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_semi<N, F>, BLOCK, smem);
     if (bs < 1) bs = 1;
-    k_stage2_semi<N><<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
+    k_stage2_semi<N, F><<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
     return cudaGetLastError();
 }
 
 // Batched form: smem = the largest tile of the batch at this multiplicity.
-template <int N>
+template <int N, bool F>
 cudaError_t launch_bs2_semi(const BatchDev* B, size_t smem, int sms, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_bstage2_semi<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_bstage2_semi<N, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr = true;
     }
     int bs = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_semi<N>, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_semi<N, F>, BLOCK, smem);
     if (bs < 1) bs = 1;
-    k_bstage2_semi<N><<<sms * bs, BLOCK, smem, st>>>(B);
+    k_bstage2_semi<N, F><<<sms * bs, BLOCK, smem, st>>>(B);
     return cudaGetLastError();
 }
 
