@@ -34,6 +34,9 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 WORKLOAD = "semilep_smeared_10M_x16"
+# DRAM bytes (read + write) of the 13 stage-2 launches of one 10M x 16 step: one ncu capture of
+# the 2M-event step (950.0 MB, dram__bytes_read.sum + dram__bytes_write.sum) scaled by the events
+STAGE2_DRAM_BYTES_PER_STEP = 4.750e9
 
 
 def _args():
@@ -262,7 +265,10 @@ def run_ours(a):
     flops = sum(cnt * flops_per_unit(n) for n, cnt in enumerate(prof["units_top"])) / max(1, prof["runs"])
     achieved = flops / (s2_ms / 1000.0) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak, traffic=None,
+    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                traffic=STAGE2_DRAM_BYTES_PER_STEP * N / N_EVENTS if V == 16 else None,
+                traffic_note="dram__bytes_read.sum + dram__bytes_write.sum of the 13 stage-2 launches of one step, "
+                             "one ncu capture at 2M events scaled to this step's events",
                 kernel="k_stage2_semi<N> (13 launches per step)", ms_per_step=s2_ms,
                 peak_note="FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
                 share_of_step=s2_ms / ms_step if ms_step else None)
