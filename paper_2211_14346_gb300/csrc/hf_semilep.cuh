@@ -46,15 +46,6 @@ __device__ __forceinline__ float chi2_band(const Plan& P, float c)
     return P.safety * (2.0f * r * d + d * d + 3.0f * u * c);
 }
 
-// Pair p of the (i < j) enumeration ordered by j, then i: p = j(j-1)/2 + i.
-__host__ __device__ constexpr int pair_j(int p)
-{
-    int j = 1;
-    while ((j + 1) * j / 2 <= p) ++j;
-    return j;
-}
-__host__ __device__ constexpr int pair_i(int p) { return p - pair_j(p) * (pair_j(p) - 1) / 2; }
-
 // Event stride of the packed Gram matrices of a tile (shared memory): odd, so
 // that lanes reading the same entry of different events hit different banks.
 __host__ __device__ constexpr int gram_stride(int n) { return ntri(n) | 1; }
