@@ -335,7 +335,7 @@ hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
  *     host threads without ordering) race and give wrong results: order them.
  * Errors: HF_EINVAL, HF_ECUDA. */
 #define HF_NOALLOC_MAX_EVENTS 1048576u
-#define HF_NOALLOC_SCRATCH_BYTES 12067840u
+#define HF_NOALLOC_SCRATCH_BYTES 13640704u
 hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const hf_columns* dev_cols, uint64_t n_events,
                                 uint64_t first_event_id, uint64_t seed, uint32_t n_variations,
                                 const hf_results* dev_out, void* stream);

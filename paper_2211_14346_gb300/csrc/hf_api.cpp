@@ -76,7 +76,7 @@ struct Analysis {
 // Layout of the device memory of one run (scratch + optional columns +
 // optional results), carved from one allocation.
 struct RunLayout {
-    size_t off_small = 0, off_bucket = 0, off_rc = 0, off_pend_cnt = 0, off_pend_left = 0, off_pend_sum = 0,
+    size_t off_small = 0, off_bucket = 0, off_rc = 0, off_pend_cnt = 0, off_pend_rng = 0, off_pend_sum = 0, off_rc_reco = 0, off_rc_pass = 0,
            off_pend_comp = 0, off_stats = 0, off_cutflow = 0, off_hist = 0, off_rctot = 0;
     size_t scratch_bytes = 0;
     unsigned rc_cap = 0;
@@ -98,12 +98,16 @@ RunLayout layout_for(uint64_t N, uint32_t V)
     o += sizeof(RcEntry) * cap;
     L.off_pend_cnt = o = align_up(o, 256);
     o += 4 * cap;
-    L.off_pend_left = o = align_up(o, 256);
-    o += 4 * cap;
+    L.off_pend_rng = o = align_up(o, 256);
+    o += 8 * cap;
     L.off_pend_sum = o = align_up(o, 256);
     o += 16 * cap;
     L.off_pend_comp = o = align_up(o, 256);
     o += 16 * cap;
+    L.off_rc_reco = o = align_up(o, 256);
+    o += 16 * cap;
+    L.off_rc_pass = o = align_up(o, 256);
+    o += 4 * cap;
     L.off_stats = o = align_up(o, 256);
     o += 8 * 3 * MAX_CUTS;
     L.off_cutflow = o = align_up(o, 256);
@@ -135,7 +139,9 @@ Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
     S.rc = (RcEntry*)(base + L.off_rc);
     S.rc_cap = L.rc_cap;
     S.pend_cnt = (unsigned*)(base + L.off_pend_cnt);
-    S.pend_left = (unsigned*)(base + L.off_pend_left);
+    S.pend_rng = (uint2*)(base + L.off_pend_rng);
+    S.rc_reco = (float4*)(base + L.off_rc_reco);
+    S.rc_pass = (unsigned*)(base + L.off_rc_pass);
     S.pend_sum = (float4*)(base + L.off_pend_sum);
     S.pend_comp = (float4*)(base + L.off_pend_comp);
     S.stats = (unsigned long long*)(base + L.off_stats);
@@ -975,7 +981,7 @@ namespace {
 
 struct BatchLayout {
     size_t off_dev, off_ch, off_plans, off_exec, off_stats, off_tpre, off_cnt, off_tctr, off_fb, off_bucket, off_rc,
-        off_pend_cnt, off_pend_left, off_pend_sum, off_pend_comp, bytes;
+        off_pend_cnt, off_pend_rng, off_pend_sum, off_pend_comp, off_rc_reco, off_rc_pass, bytes;
     size_t table_bytes;  // [off_dev, off_fb): uploaded from the host
     unsigned rc_cap;
 };
@@ -1121,12 +1127,16 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     o += sizeof(RcEntry) * cap;
     L.off_pend_cnt = o = align_up(o, 256);
     o += 4 * cap;
-    L.off_pend_left = o = align_up(o, 256);
-    o += 4 * cap;
+    L.off_pend_rng = o = align_up(o, 256);
+    o += 8 * cap;
     L.off_pend_sum = o = align_up(o, 256);
     o += 16 * cap;
     L.off_pend_comp = o = align_up(o, 256);
     o += 16 * cap;
+    L.off_rc_reco = o = align_up(o, 256);
+    o += 16 * cap;
+    L.off_rc_pass = o = align_up(o, 256);
+    o += 4 * cap;
     L.bytes = align_up(o, 256);
     // the small counter block of single runs (error word at SM_ERR) stays at the
     // arena's start, so that hf_device_error reads batches too
@@ -1170,7 +1180,9 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         S.rc = (RcEntry*)(dbase + L.off_rc);
         S.rc_cap = L.rc_cap;
         S.pend_cnt = (unsigned*)(dbase + L.off_pend_cnt);
-        S.pend_left = (unsigned*)(dbase + L.off_pend_left);
+        S.pend_rng = (uint2*)(dbase + L.off_pend_rng);
+        S.rc_reco = (float4*)(dbase + L.off_rc_reco);
+        S.rc_pass = (unsigned*)(dbase + L.off_rc_pass);
         S.pend_sum = (float4*)(dbase + L.off_pend_sum);
         S.pend_comp = (float4*)(dbase + L.off_pend_comp);
         S.stats = nullptr;

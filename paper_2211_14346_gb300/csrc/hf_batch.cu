@@ -11,6 +11,7 @@
 //   k_bstage2_*    persistent grids over the tiles of all chunks
 //                  (hf_stage2_semi.cuh, hf_stage2_dilep.cu)
 //   k_brecheck     FP64 re-evaluation of the flagged units of all chunks
+//   k_bfinish      completion of the events with rechecked units
 //
 // Every kernel reads the batch description (BatchDev, in device memory) at
 // run time and runs a grid that depends only on the GPU, so one captured
@@ -190,27 +191,25 @@ __global__ void __launch_bounds__(BLOCK) k_brecheck(const BatchDev* __restrict__
                                 &reco, &bin);
         for (int k = 0; k <= f; ++k) atomicAdd(&ch.O.cutflow[k], 1ull);
         atomicAdd(ch.O.rc_total, 1ull);
-        if (f == P.n_cuts) {
-            atomicAdd(&ch.O.hist[bin], 1ull);
-            atomicAdd(&S.pend_cnt[r.slot], 1u);
-            atomicAdd(&S.pend_sum[r.slot].x, reco.x);
-            atomicAdd(&S.pend_sum[r.slot].y, reco.y);
-            atomicAdd(&S.pend_sum[r.slot].z, reco.z);
-            atomicAdd(&S.pend_sum[r.slot].w, reco.w);
-        }
-        __threadfence();
-        const unsigned left = atomicSub(&S.pend_left[r.slot], 1u);
-        if (left == 1u) {
-            __threadfence();
-            const unsigned cnt = atomicAdd(&S.pend_cnt[r.slot], 0u);
-            float4 sum;
-            const float4 comp = S.pend_comp[r.slot];
-            sum.x = atomicAdd(&S.pend_sum[r.slot].x, 0.f);
-            sum.y = atomicAdd(&S.pend_sum[r.slot].y, 0.f);
-            sum.z = atomicAdd(&S.pend_sum[r.slot].z, 0.f);
-            sum.w = atomicAdd(&S.pend_sum[r.slot].w, 0.f);
-            write_event(ch.O, r.event, cnt, sum, comp);
-        }
+        if (f == P.n_cuts) atomicAdd(&ch.O.hist[bin], 1ull);
+        S.rc_reco[i] = reco;
+        S.rc_pass[i] = f == P.n_cuts;
+    }
+}
+
+// Completion of the pending events of all chunks, one warp per slot.
+__global__ void __launch_bounds__(BLOCK) k_bfinish(const BatchDev* __restrict__ Bp)
+{
+    const BatchDev& B = *Bp;
+    const Scratch& S = B.S;
+    const unsigned n = *S.pend_count;
+    const unsigned w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned s = w0; s < n; s += nw) {
+        unsigned cnt;
+        float4 sum, comp;
+        RcEntry first;
+        finish_pending(S, s, cnt, sum, comp, first);
+        if ((threadIdx.x & 31u) == 0) write_event(B.ch[first.chunk].O, first.event, cnt, sum, comp);
     }
 }
 
@@ -262,6 +261,7 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
         }
     }
     k_brecheck<<<L.sms * 4, BLOCK, 0, st>>>(B);
+    k_bfinish<<<L.sms * 2, BLOCK, 0, st>>>(B);
     return cudaGetLastError();
 }
 

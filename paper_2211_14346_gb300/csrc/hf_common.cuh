@@ -330,8 +330,11 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
 }
 
 // ------------------------------------------------------------------ pending events
-// An event with units in the recheck list keeps its partial result in a
-// pending slot; the last of its rechecked units writes the event's outputs.
+// An event with flagged units keeps the compensated sum of its unflagged
+// survivors in a pending slot; its flagged units go to the recheck list,
+// contiguous and in variation order.  The recheck stores each unit's FP64
+// result per entry, and the completion pass adds them to the slot's partial
+// sum in entry order (deterministic, compensated) and writes the event.
 __device__ __forceinline__ void write_event(const Out& O, uint32_t e, unsigned cnt, float4 sum, float4 comp)
 {
     if (O.mask) O.mask[e] = cnt > 0;
@@ -358,34 +361,81 @@ __device__ __forceinline__ void acc4(float4& s, float4& c, float4 x)
     two_sum(s.w, x.w, t, e); s.w = t; c.w = __fadd_rn(c.w, e);
 }
 
-// Registers an event with nflag flagged units (their variations in vs[]).
-// Falls back to evaluating them inline in FP64 when the list is full.
+// Adds the compensated sum (s2, c2) to (s, c).
+__device__ __forceinline__ void merge4(float4& s, float4& c, float4 s2, float4 c2)
+{
+    float t, e;
+    two_sum(s.x, s2.x, t, e); s.x = t; c.x = __fadd_rn(__fadd_rn(c.x, c2.x), e);
+    two_sum(s.y, s2.y, t, e); s.y = t; c.y = __fadd_rn(__fadd_rn(c.y, c2.y), e);
+    two_sum(s.z, s2.z, t, e); s.z = t; c.z = __fadd_rn(__fadd_rn(c.z, c2.z), e);
+    two_sum(s.w, s2.w, t, e); s.w = t; c.w = __fadd_rn(__fadd_rn(c.w, c2.w), e);
+}
+
+__device__ __forceinline__ float4 shfl_down4(float4 a, int o)
+{
+    a.x = __shfl_down_sync(0xffffffffu, a.x, o);
+    a.y = __shfl_down_sync(0xffffffffu, a.y, o);
+    a.z = __shfl_down_sync(0xffffffffu, a.z, o);
+    a.w = __shfl_down_sync(0xffffffffu, a.w, o);
+    return a;
+}
+
+// Warp-wide compensated sum and count (fixed tree, lane 0 holds the totals);
+// every lane of the warp must call it.
+__device__ __forceinline__ void warp_merge4(float4& s, float4& c, unsigned& n)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float4 s2 = shfl_down4(s, o), c2 = shfl_down4(c, o);
+        const unsigned n2 = __shfl_down_sync(0xffffffffu, n, o);
+        merge4(s, c, s2, c2);
+        n += n2;
+    }
+}
+
+// Reserves nflag recheck entries and a pending slot for event e (one thread).
+// Returns false when the list is full (the entries must then be evaluated
+// by the caller).
+__device__ __forceinline__ bool reserve_pending(const Scratch& S, unsigned nflag, unsigned cnt, float4 sum,
+                                                float4 comp, unsigned& base, unsigned& slot)
+{
+    base = atomicAdd(S.rc_count, nflag);
+    if (base + nflag > S.rc_cap) {
+        atomicOr(S.err, ERR_RECHECK_FULL);
+        return false;
+    }
+    // entries below the largest end of a successful reservation are all
+    // written; every reservation after a failed one fails too
+    atomicMax(S.rc_valid, base + nflag);
+    slot = atomicAdd(S.pend_count, 1u);
+    S.pend_cnt[slot] = cnt;
+    S.pend_rng[slot] = make_uint2(base, nflag);
+    S.pend_sum[slot] = sum;
+    S.pend_comp[slot] = comp;
+    return true;
+}
+
+__device__ __forceinline__ RcEntry rc_entry(const Scratch& S, uint32_t e, uint32_t v, unsigned s1bits, unsigned slot)
+{
+    RcEntry r;
+    r.event = e;
+    r.vbits = v | (s1bits << 16);
+    r.slot = slot;
+    r.chunk = S.chunk;
+    return r;
+}
+
+// Registers an event with nflag flagged units (their variations in vs[], in
+// increasing order).  Evaluates them here in FP64 when the list is full.
 static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t e,
                            uint64_t event_id, uint64_t seed, unsigned s1bits, unsigned cnt, float4 sum,
                            float4 comp, const uint16_t* vs, int nflag, unsigned long long* fc, unsigned* hist)
 {
-    unsigned base = atomicAdd(S.rc_count, (unsigned)nflag);
-    if (base + (unsigned)nflag <= S.rc_cap) {
-        // entries below the largest end of a successful reservation are all
-        // written; a reservation crossing rc_cap is never written
-        atomicMax(S.rc_valid, base + (unsigned)nflag);
-        unsigned slot = atomicAdd(S.pend_count, 1u);
-        S.pend_cnt[slot] = cnt;
-        S.pend_left[slot] = (unsigned)nflag;
-        S.pend_sum[slot] = sum;
-        S.pend_comp[slot] = comp;
-        for (int i = 0; i < nflag; ++i) {
-            RcEntry r;
-            r.event = e;
-            r.vbits = (uint32_t)vs[i] | (s1bits << 16);
-            r.slot = slot;
-            r.chunk = S.chunk;
-            S.rc[base + i] = r;
-        }
+    unsigned base, slot;
+    if (reserve_pending(S, (unsigned)nflag, cnt, sum, comp, base, slot)) {
+        for (int i = 0; i < nflag; ++i) S.rc[base + i] = rc_entry(S, e, vs[i], s1bits, slot);
         return;
     }
-    // list full: evaluate here (slow, correct)
-    atomicOr(S.err, ERR_RECHECK_FULL);
     for (int i = 0; i < nflag; ++i) {
         float4 reco;
         int bin = 0;
@@ -399,6 +449,33 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
     }
     atomicAdd(O.rc_total, (unsigned long long)nflag);
     write_event(O, e, cnt, sum, comp);
+}
+
+// Completion of pending slot s by one warp: the unflagged partial sum plus the
+// passing entries' FP64 results.  Lane 0 returns the totals and the event.
+__device__ __forceinline__ void finish_pending(const Scratch& S, unsigned s, unsigned& cnt, float4& sum, float4& comp,
+                                               RcEntry& first)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const uint2 rg = S.pend_rng[s];
+    sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    comp = sum;
+    cnt = 0;
+    for (unsigned i = lane; i < rg.y; i += 32) {
+        if (S.rc_pass[rg.x + i]) {
+            ++cnt;
+            acc4(sum, comp, S.rc_reco[rg.x + i]);
+        }
+    }
+    warp_merge4(sum, comp, cnt);
+    if (lane == 0) {
+        float4 ps = S.pend_sum[s], pc = S.pend_comp[s];
+        merge4(ps, pc, sum, comp);
+        sum = ps;
+        comp = pc;
+        cnt += S.pend_cnt[s];
+        first = S.rc[rg.x];
+    }
 }
 
 // ------------------------------------------------------------------ tile epilogues
@@ -431,46 +508,102 @@ __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsi
     }
 }
 
-// Per-event reduction of a tile's units, one thread per event, in variation
-// order: compensated sums of the surviving units' reconstructed quantities;
-// events without flagged units are written, the others are registered for
-// the FP64 recheck (more than 64 flagged units: the excess is evaluated here).
+// Per-event reduction of a tile's units: compensated sums of the surviving
+// units' reconstructed quantities; events without flagged units are written,
+// the others get a pending slot and their flagged units go to the recheck
+// list.  Fewer than 32 variations: one thread per event, in variation order;
+// otherwise one warp per event (lanes strided over the variations, a fixed
+// combining tree), so that a single event of up to 4096 variations does not
+// serialise the tile.  rank and size describe the calling group (size a
+// multiple of 32, every thread calls).
 __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                                           uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
                                           const uint32_t* bits, const int* uf, const float4* ureco,
                                           unsigned long long* fc, unsigned* hist, int rank, int size)
 {
-    for (int ev = rank; ev < ne; ev += size) {
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
-        unsigned cnt = 0;
-        int nflag = 0;
-        uint16_t vs[64];
-        const uint32_t e = evid[ev];
-        for (uint32_t v = 0; v < V; ++v) {
-            const int u = ev * (int)V + (int)v;
-            const int f = uf[u];
-            if (f < 0) {
-                if (nflag < 64) {
+    if (V < 32) {
+        for (int ev = rank; ev < ne; ev += size) {
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
+            unsigned cnt = 0;
+            int nflag = 0;
+            uint16_t vs[32];
+            const uint32_t e = evid[ev];
+            for (uint32_t v = 0; v < V; ++v) {
+                const int u = ev * (int)V + (int)v;
+                const int f = uf[u];
+                if (f < 0) {
                     vs[nflag++] = (uint16_t)v;
-                } else {
-                    float4 reco;
-                    int bin = 0;
-                    int f2 = unit_fp64(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin);
-                    atomicAdd(&fc[f2], 1ull);
-                    atomicAdd(O.rc_total, 1ull);
-                    if (f2 == P.n_cuts) {
-                        ++cnt;
-                        atomicAdd(&hist[bin], 1u);
-                        acc4(sum, comp, reco);
-                    }
+                } else if (f == P.n_cuts) {
+                    ++cnt;
+                    acc4(sum, comp, ureco[u]);
                 }
-            } else if (f == P.n_cuts) {
+            }
+            if (nflag == 0) write_event(O, e, cnt, sum, comp);
+            else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
+        }
+        return;
+    }
+    const unsigned lane = (unsigned)rank & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    for (int ev = rank >> 5; ev < ne; ev += size >> 5) {
+        const uint32_t e = evid[ev];
+        const int u0 = ev * (int)V;
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
+        unsigned cnt = 0, nflag = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += 32) {
+            const uint32_t v = v0 + lane;
+            const int f = v < V ? uf[u0 + (int)v] : 0;
+            nflag += __popc(__ballot_sync(0xffffffffu, v < V && f < 0));
+            if (v < V && f == P.n_cuts) {
                 ++cnt;
-                acc4(sum, comp, ureco[u]);
+                acc4(sum, comp, ureco[u0 + (int)v]);
             }
         }
-        if (nflag == 0) write_event(O, e, cnt, sum, comp);
-        else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
+        warp_merge4(sum, comp, cnt);
+        if (nflag == 0) {
+            if (lane == 0) write_event(O, e, cnt, sum, comp);
+            continue;
+        }
+        unsigned base = 0, slot = 0;
+        int ok = 0;
+        if (lane == 0) ok = reserve_pending(S, nflag, cnt, sum, comp, base, slot);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (ok) {
+            for (uint32_t v0 = 0; v0 < V; v0 += 32) {
+                const uint32_t v = v0 + lane;
+                const bool fl = v < V && uf[u0 + (int)v] < 0;
+                const unsigned m = __ballot_sync(0xffffffffu, fl);
+                if (fl) S.rc[base + __popc(m & below)] = rc_entry(S, e, v, bits[ev], slot);
+                base += __popc(m);
+            }
+            continue;
+        }
+        // list full: the lanes evaluate the flagged units in FP64
+        float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = s2;
+        unsigned n2 = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += 32) {
+            const uint32_t v = v0 + lane;
+            if (v < V && uf[u0 + (int)v] < 0) {
+                float4 reco;
+                int bin = 0;
+                const int f2 = unit_fp64(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin);
+                atomicAdd(&fc[f2], 1ull);
+                if (f2 == P.n_cuts) {
+                    ++n2;
+                    atomicAdd(&hist[bin], 1u);
+                    acc4(s2, c2, reco);
+                }
+            }
+        }
+        __syncwarp();
+        warp_merge4(s2, c2, n2);
+        if (lane == 0) {
+            merge4(sum, comp, s2, c2);
+            atomicAdd(O.rc_total, (unsigned long long)nflag);
+            write_event(O, e, cnt + n2, sum, comp);
+        }
     }
 }
 

@@ -106,12 +106,14 @@ struct Scratch {
     unsigned* pend_count; // [1]  pending-event slots used
     unsigned* err;        // [1]  error word
     uint2* bucket;        // [N]  stage-2 work: (event, stage-1 bits), grouped by n
-    RcEntry* rc;          // [rc_cap]
+    RcEntry* rc;          // [rc_cap] flagged units; those of one event are contiguous, in variation order
     unsigned rc_cap;
-    unsigned* pend_cnt;   // [rc_cap] surviving units so far (pending events)
-    unsigned* pend_left;  // [rc_cap] flagged units still to recheck
-    float4* pend_sum;     // [rc_cap] partial sums of reco (float, then final)
-    float4* pend_comp;    // [rc_cap] compensation terms of the partial sums
+    float4* rc_reco;      // [rc_cap] FP64 result of entry i: reconstructed quantities
+    unsigned* rc_pass;    // [rc_cap] FP64 result of entry i: 1 if the unit passes every cut
+    unsigned* pend_cnt;   // [rc_cap] surviving unflagged units of pending event s
+    uint2* pend_rng;      // [rc_cap] (first entry, number of entries) of pending event s
+    float4* pend_sum;     // [rc_cap] compensated sum over the unflagged survivors
+    float4* pend_comp;    // [rc_cap] its compensation terms
     unsigned long long* stats;  // [3*MAX_CUTS] evaluated, passed, cost (cycles)
     unsigned long long* prof;   // [64] profiling counters (PROF_*) or null
     const int* exec2;     // [MAX_CUTS] device execution order of stage-2 cuts (or null)

@@ -10,8 +10,8 @@
 //                (shared-memory counters, one global atomic per bucket per block)
 //   k_stage2_*<N> one persistent grid per jet multiplicity N, largest first
 //                (hf_stage2_semi.cuh)
-//   k_recheck    FP64 re-evaluation of the listed units, then completion of
-//                their events
+//   k_recheck    FP64 re-evaluation of the listed units
+//   k_finish     completion of the events with rechecked units
 // Cut flow and histogram are integer counts reduced in shared memory and
 // added to global u64 counters once per block.
 #include "hf_common.cuh"
@@ -106,31 +106,29 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
         int f = unit_fp64(P, C, r.event, first_id + r.event, seed, r.vbits & 0xffffu, r.vbits >> 16, &reco, &bin);
         ++mine;
         atomicAdd(&s_fc[f], 1ull);
-        if (f == P.n_cuts) {
-            atomicAdd(&s_hist[bin], 1u);
-            atomicAdd(&S.pend_cnt[r.slot], 1u);
-            atomicAdd(&S.pend_sum[r.slot].x, reco.x);
-            atomicAdd(&S.pend_sum[r.slot].y, reco.y);
-            atomicAdd(&S.pend_sum[r.slot].z, reco.z);
-            atomicAdd(&S.pend_sum[r.slot].w, reco.w);
-        }
-        __threadfence();
-        unsigned left = atomicSub(&S.pend_left[r.slot], 1u);
-        if (left == 1u) {
-            __threadfence();
-            unsigned cnt = atomicAdd(&S.pend_cnt[r.slot], 0u);
-            float4 sum, comp = S.pend_comp[r.slot];
-            sum.x = atomicAdd(&S.pend_sum[r.slot].x, 0.f);
-            sum.y = atomicAdd(&S.pend_sum[r.slot].y, 0.f);
-            sum.z = atomicAdd(&S.pend_sum[r.slot].z, 0.f);
-            sum.w = atomicAdd(&S.pend_sum[r.slot].w, 0.f);
-            write_event(O, r.event, cnt, sum, comp);
-        }
+        if (f == P.n_cuts) atomicAdd(&s_hist[bin], 1u);
+        S.rc_reco[i] = reco;
+        S.rc_pass[i] = f == P.n_cuts;
     }
     if (mine) atomicAdd(O.rc_total, mine);
     __syncthreads();
     flush_cutflow(P, O, s_fc);
     flush_hist(P, O, s_hist);
+}
+
+// ------------------------------------------------------------------ k_finish
+// Completion of the pending events after the recheck, one warp per slot.
+__global__ void __launch_bounds__(BLOCK) k_finish(const Out O, Scratch S)
+{
+    const unsigned n = *S.pend_count;
+    const unsigned w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned s = w0; s < n; s += nw) {
+        unsigned cnt;
+        float4 sum, comp;
+        RcEntry first;
+        finish_pending(S, s, cnt, sum, comp, first);
+        if ((threadIdx.x & 31u) == 0) write_event(O, first.event, cnt, sum, comp);
+    }
 }
 
 // ------------------------------------------------------------------ host launchers
@@ -206,6 +204,7 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
         if (ev) cudaEventRecord(ev[2], st);
     }
     k_recheck<<<sms * 4, BLOCK, 0, st>>>(P, C, O, S, seed, first_id);
+    k_finish<<<sms * 2, BLOCK, 0, st>>>(O, S);
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }

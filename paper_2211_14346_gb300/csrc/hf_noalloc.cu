@@ -30,10 +30,12 @@ constexpr size_t NA_SMALL = 0;                                      // counters,
 constexpr size_t NA_BUCKET = 256;                                   // uint2[NA_MAX_EVENTS]
 constexpr size_t NA_RC = NA_BUCKET + 8 * NA_MAX_EVENTS;             // RcEntry[NA_RC_CAP]
 constexpr size_t NA_PEND_CNT = NA_RC + 16 * (size_t)NA_RC_CAP;      // unsigned[NA_RC_CAP]
-constexpr size_t NA_PEND_LEFT = NA_PEND_CNT + 4 * (size_t)NA_RC_CAP;
-constexpr size_t NA_PEND_SUM = NA_PEND_LEFT + 4 * (size_t)NA_RC_CAP;  // float4[NA_RC_CAP]
+constexpr size_t NA_PEND_RNG = NA_PEND_CNT + 4 * (size_t)NA_RC_CAP;   // uint2[NA_RC_CAP]
+constexpr size_t NA_PEND_SUM = NA_PEND_RNG + 8 * (size_t)NA_RC_CAP;   // float4[NA_RC_CAP]
 constexpr size_t NA_PEND_COMP = NA_PEND_SUM + 16 * (size_t)NA_RC_CAP;
-constexpr size_t NA_CUTFLOW = NA_PEND_COMP + 16 * (size_t)NA_RC_CAP;  // u64[MAX_CUTS+1]
+constexpr size_t NA_RC_RECO = NA_PEND_COMP + 16 * (size_t)NA_RC_CAP;  // float4[NA_RC_CAP]
+constexpr size_t NA_RC_PASS = NA_RC_RECO + 16 * (size_t)NA_RC_CAP;    // unsigned[NA_RC_CAP]
+constexpr size_t NA_CUTFLOW = NA_RC_PASS + 4 * (size_t)NA_RC_CAP;     // u64[MAX_CUTS+1]
 constexpr size_t NA_HIST = NA_CUTFLOW + 256;                          // u64[MAX_BINS+2]
 constexpr size_t NA_RCTOT = NA_HIST + 8 * (MAX_BINS + 2 + 30);        // u64
 constexpr size_t NA_BYTES = NA_RCTOT + 256;
@@ -112,7 +114,9 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
     S.rc = (RcEntry*)(base + NA_RC);
     S.rc_cap = NA_RC_CAP;
     S.pend_cnt = (unsigned*)(base + NA_PEND_CNT);
-    S.pend_left = (unsigned*)(base + NA_PEND_LEFT);
+    S.pend_rng = (uint2*)(base + NA_PEND_RNG);
+    S.rc_reco = (float4*)(base + NA_RC_RECO);
+    S.rc_pass = (unsigned*)(base + NA_RC_PASS);
     S.pend_sum = (float4*)(base + NA_PEND_SUM);
     S.pend_comp = (float4*)(base + NA_PEND_COMP);
     S.stats = nullptr;  // no scheduler: user order

@@ -79,6 +79,12 @@ def config3():
     return dilep(sigma_jet=0.10, sigma_met=10.0)
 
 
+def tth_sci():
+    """The paper's ttH_sci resolution model on the dilepton chain: 1 % jet
+    energy resolution, MET shifted by N(0, 1 GeV) per component."""
+    return dilep(sigma_jet=0.01, sigma_met=1.0)
+
+
 def with_cuts(an, cuts):
     out = copy.deepcopy(an)
     out["cuts"] = list(cuts)
