@@ -133,7 +133,30 @@ typedef struct {
     float sigma_met;     /* absolute MET resolution per component, GeV, >= 0           */
     uint32_t hist_nbins; /* reconstructed-mass histogram: bins, 1..1024                */
     float hist_lo, hist_hi; /* range, GeV; hist_lo < hist_hi                            */
+    uint32_t record_levels; /* per-cut variable recording (Sect. 3): bit k records the
+                               events that pass cuts 0..k (user order) in at least one
+                               variation; 0 = no recording; bits >= n_cuts are invalid  */
+    uint32_t record_vars[4]; /* HF_VAR_* stored in hf_record.value[0..3]               */
 } hf_analysis_desc;
+
+/* Variables of the per-cut recording.  A variable is stored at every
+ * recorded level; where it is not defined yet at that level it holds its
+ * default, 0 (Sect. 3: variables not yet updated keep their default). */
+#define HF_VAR_NONE 0u    /* always 0                                                    */
+#define HF_VAR_NJETS 1u   /* number of jets                                              */
+#define HF_VAR_NBTAG 2u   /* number of b-tagged jets                                     */
+#define HF_VAR_LEP_PT 3u  /* pT of the event's first lepton, GeV (FP64, rounded to float) */
+#define HF_VAR_MET 4u     /* |MET| as measured (not smeared), GeV (FP64, rounded to float) */
+#define HF_VAR_RECO0 5u   /* hf_results.reco[0..3] (+0..3): defined at the last cut only */
+#define HF_VAR_RECO3 8u
+
+/* One record: event (index within the chunk) e passes cuts 0..level in at
+ * least one variation.  24 bytes. */
+typedef struct {
+    uint32_t event;
+    uint32_t level;
+    float value[4];
+} hf_record;
 
 /* Validates and registers an analysis.  *analysis_id receives its id.
  * Errors: HF_EINVAL (unknown kind, n_cuts out of range, missing
@@ -164,6 +187,11 @@ typedef struct {
                            fit (m_top had, m_top lep, pz_nu, |MET|) --, dilepton
                            (m_bb, m_t, m_tbar, m_ttbar); zeros when n_surv = 0           */
     uint64_t* recheck_count; /* 1: units re-evaluated in FP64 (diagnostic)              */
+    hf_record* records; /* per-cut records of an analysis with record_levels != 0, in no
+                           particular order; device memory (the device-resident entry
+                           points only: hf_submit_chunk / hf_fetch_results reject it)    */
+    uint64_t record_cap; /* records entries; records beyond it are counted, not written */
+    uint64_t* n_records; /* 1 (device): records produced (may exceed record_cap)         */
 } hf_results;
 
 /* Asynchronous chunk submission (the serving entry point).  Admission: the
@@ -335,7 +363,7 @@ hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
  *     host threads without ordering) race and give wrong results: order them.
  * Errors: HF_EINVAL, HF_ECUDA. */
 #define HF_NOALLOC_MAX_EVENTS 1048576u
-#define HF_NOALLOC_SCRATCH_BYTES 13640704u
+#define HF_NOALLOC_SCRATCH_BYTES 14722304u
 hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const hf_columns* dev_cols, uint64_t n_events,
                                 uint64_t first_event_id, uint64_t seed, uint32_t n_variations,
                                 const hf_results* dev_out, void* stream);

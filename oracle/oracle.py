@@ -160,6 +160,64 @@ def run(an, cols, *, seed=0, V=1, first_event_id=0, unit_passed=False):
     return out
 
 
+RECORD_VARS = ("none", "njets", "nbtag", "lep_pt", "met", "reco0", "reco1", "reco2", "reco3")
+
+
+def records(an, cols, *, seed=0, V=1, first_event_id=0):
+    """Per-cut variable records (Sect. 3: the variables the user chose are
+    stored at every selection level, holding their default where not yet
+    updated; Sect. 6.1 example).  an["record"] = dict(levels=[k, ...],
+    vars=[name, ...]) with names from RECORD_VARS.
+
+    Event e is recorded at level k when some variation of it passes cuts
+    0..k in user order, i.e. when the most leading cuts passed by any of its
+    variations exceeds k.  The recorded values are the event's number of
+    jets, number of b-tagged jets, first-lepton pT and measured |MET| (FP64,
+    rounded to float), and at the last level only the per-event mean
+    reconstructed quantities (0 below it).  Returns a dict: event (u32),
+    level (u32), value (f64[n, 4]; the reco slots as the FP64 means), sorted
+    by (event, level), and the run's result dict."""
+    rec = an["record"]
+    levels = sorted(set(int(k) for k in rec["levels"]))
+    names = list(rec.get("vars", ())) + ["none"] * (4 - len(rec.get("vars", ())))
+    r = run(an, cols, seed=seed, V=V, first_event_id=first_event_id, unit_passed=True)
+    N = cols.n_events
+    maxf = r["unit_passed"].astype(np.int64).max(axis=1) if N else np.zeros(0, np.int64)
+    n = np.diff(np.asarray(cols.jet_off, dtype=np.int64))
+    btag = np.asarray(cols.btag, dtype=np.int64)
+    nb = np.array([bin(int(b) & ((1 << int(k)) - 1)).count("1") for b, k in zip(btag, n)], dtype=np.int64)
+    lep = np.asarray(cols.lep, dtype=np.float32).reshape(N, cols.n_lep, 4)[:, 0, :].astype(np.float64)
+    met = np.asarray(cols.met, dtype=np.float32).reshape(N, 2).astype(np.float64)
+    lep_pt = np.sqrt(lep[:, 0] * lep[:, 0] + lep[:, 1] * lep[:, 1]).astype(np.float32)
+    met_abs = np.sqrt(met[:, 0] * met[:, 0] + met[:, 1] * met[:, 1]).astype(np.float32)
+    last = len(an["cuts"]) - 1
+    ev, lv, val = [], [], []
+    for e in range(N):
+        for k in levels:
+            if maxf[e] <= k:
+                continue
+            row = []
+            for name in names:
+                if name == "njets":
+                    x = float(n[e])
+                elif name == "nbtag":
+                    x = float(nb[e])
+                elif name == "lep_pt":
+                    x = float(lep_pt[e])
+                elif name == "met":
+                    x = float(met_abs[e])
+                elif name.startswith("reco"):
+                    x = float(r["reco"][e, int(name[4])]) if k == last else 0.0
+                else:
+                    x = 0.0
+                row.append(x)
+            ev.append(e)
+            lv.append(k)
+            val.append(row)
+    return dict(event=np.asarray(ev, np.uint32), level=np.asarray(lv, np.uint32),
+                value=np.asarray(val, np.float64).reshape(-1, 4), run=r)
+
+
 def unit(an, cols, e, v, *, seed=0, first_event_id=0):
     """One unit (event e, variation v): dict(passed, idx[4], q[6])."""
     lib = load()

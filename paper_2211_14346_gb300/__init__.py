@@ -134,10 +134,15 @@ class HostColumnsView:
         return columns_struct([a.ctypes.data for a in self._keep], self.n_jets_total)
 
 
-class DeviceResults:
-    """Device result buffers of one run (torch CUDA tensors)."""
+# host layout of hf_record
+RECORD_DTYPE = np.dtype([("event", "<u4"), ("level", "<u4"), ("value", "<f4", (4,))])
 
-    def __init__(self, n_events, n_cuts, nbins, device="cuda"):
+
+class DeviceResults:
+    """Device result buffers of one run (torch CUDA tensors); record_cap > 0
+    adds the per-cut record buffer (24-byte hf_record entries)."""
+
+    def __init__(self, n_events, n_cuts, nbins, device="cuda", record_cap=0):
         import torch
         self.mask = torch.zeros(n_events, dtype=torch.uint8, device=device)
         self.cutflow = torch.zeros(n_cuts + 1, dtype=torch.int64, device=device)
@@ -145,19 +150,58 @@ class DeviceResults:
         self.n_surv = torch.zeros(n_events, dtype=torch.int16, device=device)
         self.reco = torch.zeros((n_events, N_RECO), dtype=torch.float32, device=device)
         self.recheck_count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.record_cap = int(record_cap)
+        self.records = torch.zeros((max(1, self.record_cap), 6), dtype=torch.int32, device=device) \
+            if self.record_cap else None
+        self.n_records = torch.zeros(1, dtype=torch.int64, device=device) if self.record_cap else None
 
     def struct(self, fields=None):
         s = _lib.hf_results()
         for f in ("mask", "cutflow", "hist", "n_surv", "reco", "recheck_count"):
             if fields is None or f in fields:
                 setattr(s, f, getattr(self, f).data_ptr())
+        if self.records is not None and (fields is None or "records" in fields):
+            s.records = self.records.data_ptr()
+            s.record_cap = self.record_cap
+            s.n_records = self.n_records.data_ptr()
         return s
 
     def numpy(self):
-        return dict(mask=self.mask.cpu().numpy(), cutflow=self.cutflow.cpu().numpy().astype(np.uint64),
-                    hist=self.hist.cpu().numpy().astype(np.uint64),
-                    n_surv=self.n_surv.cpu().numpy().view(np.uint16), reco=self.reco.cpu().numpy(),
-                    recheck_count=int(self.recheck_count.cpu().item()))
+        out = dict(mask=self.mask.cpu().numpy(), cutflow=self.cutflow.cpu().numpy().astype(np.uint64),
+                   hist=self.hist.cpu().numpy().astype(np.uint64),
+                   n_surv=self.n_surv.cpu().numpy().view(np.uint16), reco=self.reco.cpu().numpy(),
+                   recheck_count=int(self.recheck_count.cpu().item()))
+        if self.records is not None:
+            n = int(self.n_records.cpu().item())
+            raw = self.records[:min(n, self.record_cap)].cpu().numpy()
+            rec = np.ascontiguousarray(raw).view(RECORD_DTYPE).reshape(-1)
+            out["n_records"] = n
+            # the kernels append in no particular order; sorted by (event, level) here
+            out["records"] = rec[np.lexsort((rec["level"], rec["event"]))]
+        return out
+
+
+def analysis_desc(an):
+    """hf_analysis_desc of a user-level analysis dict (see synth.analyses);
+    returns (desc, cuts): keep cuts alive while desc is in use."""
+    cuts = _cut_struct(an["cuts"])
+    d = _lib.hf_analysis_desc()
+    d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
+    d.n_cuts = len(an["cuts"])
+    d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
+    for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
+        setattr(d, k, _f32(an[k]))
+    nb, lo, hi = an["hist"]
+    d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
+    rec = an.get("record")
+    if rec:
+        d.record_levels = sum(1 << int(k) for k in rec["levels"])
+        vs = list(rec.get("vars", ()))
+        if len(vs) > 4:
+            raise ValueError("at most 4 recorded variables")
+        for i, v in enumerate(vs):
+            d.record_vars[i] = _lib.HF_VAR[v]
+    return d, cuts
 
 
 class Engine:
@@ -187,23 +231,21 @@ class Engine:
 
     def define(self, an) -> int:
         """Registers a user-level analysis (see synth.analyses).  Returns its id."""
-        cuts = _cut_struct(an["cuts"])
-        d = _lib.hf_analysis_desc()
-        d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
-        d.n_cuts = len(an["cuts"])
-        d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
-        for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
-            setattr(d, k, _f32(an[k]))
-        nb, lo, hi = an["hist"]
-        d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
+        d, cuts = analysis_desc(an)
         aid = C.c_uint32()
         self._check(self.lib.hf_define_cuts(self.ctx, C.byref(d), C.byref(aid)))
         self._analyses[aid.value] = an
         return aid.value
 
-    def results_for(self, aid, n_events, device="cuda"):
+    def results_for(self, aid, n_events, device="cuda", record_cap=None):
+        """Result buffers for a run of analysis aid; an analysis that records
+        gets room for every possible record (n_events per recorded level)
+        unless record_cap says otherwise."""
         an = self._analyses[aid]
-        return DeviceResults(n_events, len(an["cuts"]), an["hist"][0], device)
+        if record_cap is None:
+            rec = an.get("record")
+            record_cap = n_events * len(set(rec["levels"])) if rec else 0
+        return DeviceResults(n_events, len(an["cuts"]), an["hist"][0], device, record_cap)
 
     def run_device(self, aid, dcols, *, V=1, seed=0, first_event_id=0, out=None, plain=False, stream=None,
                    fields=None):

@@ -47,11 +47,16 @@ class hf_cut(C.Structure):
                 ("reorderable", C.c_uint8), ("pad", C.c_uint8 * 3)]
 
 
+# variables of the per-cut recording (HF_VAR_*)
+HF_VAR = {"none": 0, "njets": 1, "nbtag": 2, "lep_pt": 3, "met": 4, "reco0": 5, "reco1": 6, "reco2": 7, "reco3": 8}
+
+
 class hf_analysis_desc(C.Structure):
     _fields_ = [("event_model", C.c_int32), ("n_cuts", C.c_uint32), ("cuts", C.POINTER(hf_cut)),
                 ("mW", C.c_float), ("mt", C.c_float), ("sigma_t", C.c_float), ("sigma_W", C.c_float),
                 ("mH", C.c_float), ("sigma_jet", C.c_float), ("sigma_met", C.c_float),
-                ("hist_nbins", C.c_uint32), ("hist_lo", C.c_float), ("hist_hi", C.c_float)]
+                ("hist_nbins", C.c_uint32), ("hist_lo", C.c_float), ("hist_hi", C.c_float),
+                ("record_levels", C.c_uint32), ("record_vars", C.c_uint32 * 4)]
 
 
 class hf_columns(C.Structure):
@@ -61,7 +66,8 @@ class hf_columns(C.Structure):
 
 class hf_results(C.Structure):
     _fields_ = [("mask", C.c_void_p), ("cutflow", C.c_void_p), ("hist", C.c_void_p), ("n_surv", C.c_void_p),
-                ("reco", C.c_void_p), ("recheck_count", C.c_void_p)]
+                ("reco", C.c_void_p), ("recheck_count", C.c_void_p), ("records", C.c_void_p),
+                ("record_cap", C.c_uint64), ("n_records", C.c_void_p)]
 
 
 class hf_chunk(C.Structure):

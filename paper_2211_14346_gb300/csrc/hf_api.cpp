@@ -76,7 +76,8 @@ struct Analysis {
 // Layout of the device memory of one run (scratch + optional columns +
 // optional results), carved from one allocation.
 struct RunLayout {
-    size_t off_small = 0, off_bucket = 0, off_rc = 0, off_pend_cnt = 0, off_pend_rng = 0, off_pend_sum = 0, off_rc_reco = 0, off_rc_pass = 0,
+    size_t off_small = 0, off_bucket = 0, off_rc = 0, off_pend_cnt = 0, off_pend_rng = 0, off_pend_sum = 0,
+           off_rc_reco = 0, off_rc_f = 0, off_maxf = 0, off_rec_pre = 0,
            off_pend_comp = 0, off_stats = 0, off_cutflow = 0, off_hist = 0, off_rctot = 0;
     size_t scratch_bytes = 0;
     unsigned rc_cap = 0;
@@ -106,8 +107,12 @@ RunLayout layout_for(uint64_t N, uint32_t V)
     o += 16 * cap;
     L.off_rc_reco = o = align_up(o, 256);
     o += 16 * cap;
-    L.off_rc_pass = o = align_up(o, 256);
+    L.off_rc_f = o = align_up(o, 256);
     o += 4 * cap;
+    L.off_maxf = o = align_up(o, 256);
+    o += std::max<uint64_t>(N, 1);
+    L.off_rec_pre = o = align_up(o, 256);
+    o += 8 * ((N + 255) / 256 + 1);
     L.off_stats = o = align_up(o, 256);
     o += 8 * 3 * MAX_CUTS;
     L.off_cutflow = o = align_up(o, 256);
@@ -141,7 +146,8 @@ Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
     S.pend_cnt = (unsigned*)(base + L.off_pend_cnt);
     S.pend_rng = (uint2*)(base + L.off_pend_rng);
     S.rc_reco = (float4*)(base + L.off_rc_reco);
-    S.rc_pass = (unsigned*)(base + L.off_rc_pass);
+    S.rc_f = (int*)(base + L.off_rc_f);
+    S.rec_pre = (unsigned long long*)(base + L.off_rec_pre);
     S.pend_sum = (float4*)(base + L.off_pend_sum);
     S.pend_comp = (float4*)(base + L.off_pend_comp);
     S.stats = (unsigned long long*)(base + L.off_stats);
@@ -294,6 +300,9 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     if (!(d->sigma_met >= 0.0f) || !std::isfinite(d->sigma_met)) return fail(HF_EINVAL, "sigma_met must be >= 0");
     if (d->hist_nbins < 1 || d->hist_nbins > (uint32_t)MAX_BINS || !(d->hist_lo < d->hist_hi))
         return fail(HF_EINVAL, "histogram: 1..1024 bins and lo < hi");
+    if (d->record_levels >> d->n_cuts) return fail(HF_EINVAL, "record_levels names a cut level >= n_cuts");
+    for (int i = 0; i < 4; ++i)
+        if (d->record_vars[i] > HF_VAR_RECO3) return fail(HF_EINVAL, "record_vars: unknown HF_VAR_*");
     memset(&P, 0, sizeof P);
     P.model = d->event_model;
     P.n_cuts = (int)d->n_cuts;
@@ -358,6 +367,8 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     P.dsigma_met = d->sigma_met;
     P.dlo = d->hist_lo;
     P.dhi = d->hist_hi;
+    P.rec_levels = d->record_levels;
+    for (int i = 0; i < 4; ++i) P.rec_var[i] = (int)d->record_vars[i];
     // FP32 error model: normals within 2.5 ulp (bound 4e-7 relative), |z| <= 5.8;
     // jet scale s = 1 + sigma z within sigma * 4e-7 * 5.8 / (1 - 5.8 sigma) + 2^-24
     // relative; a Gram-matrix mass squared within 2 s_rel + 12 u, the mass within half of
@@ -410,6 +421,22 @@ hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
     return HF_OK;
 }
 
+// Per-cut records of a device-resident run: only for an analysis that
+// records, with a counter to receive their number.
+hf_status records_out(const Analysis& A, const hf_results& r, Out& O)
+{
+    if (!r.records || !A.plan.rec_levels) return HF_OK;
+    if (!r.n_records) return fail(HF_EINVAL, "records given without n_records");
+    if ((uintptr_t)r.records & 3) return fail(HF_EINVAL, "records must be 4-byte aligned");
+    for (int i = 0; i < 4; ++i)
+        if (A.plan.rec_var[i] >= VAR_RECO0 && !r.reco)
+            return fail(HF_EINVAL, "recording a reconstructed quantity needs the reco output");
+    O.rec = (Record*)r.records;
+    O.rec_cap = r.record_cap;
+    O.n_rec = (unsigned long long*)r.n_records;
+    return HF_OK;
+}
+
 // Enqueues one run on stream st with the device memory at `scratch`.
 hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint32_t V, const Out& Oin,
                       char* scratch, const RunLayout& L, uint64_t seed, uint64_t first_id, bool plain,
@@ -425,6 +452,10 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
     HF_CUDA(cudaMemsetAsync(O.cutflow, 0, 8 * (A.plan.n_cuts + 1), st));
     HF_CUDA(cudaMemsetAsync(O.hist, 0, 8 * (A.plan.nbins + 2), st));
     HF_CUDA(cudaMemsetAsync(O.rc_total, 0, 8, st));
+    if (O.rec) {
+        O.maxf = (uint8_t*)(scratch + L.off_maxf);
+        HF_CUDA(cudaMemsetAsync(O.n_rec, 0, 8, st));
+    }
     if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per call");
     if (N == 0) return HF_OK;
     bool use_plain = plain || (ctx->flags & HF_FLAG_PLAIN);
@@ -498,6 +529,7 @@ hf_status run_device_impl(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* d
         O.hist = (unsigned long long*)dev_out->hist;
         O.rc_total = (unsigned long long*)dev_out->recheck_count;
         if (dev_out->reco && ((uintptr_t)dev_out->reco & 15)) return fail(HF_EINVAL, "reco must be 16-byte aligned");
+        if (hf_status rs = records_out(*A, *dev_out, O)) return rs;
     }
     hf_status s = enqueue_run(ctx, *A, C, N, V, O, ctx->arena, RL, seed, first_event_id, plain, st);
     if (s) return s;
@@ -782,6 +814,8 @@ hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state)
 hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32_t timeout_ms)
 {
     if (!ctx) return fail(HF_EINVAL, "ctx is NULL");
+    if (out && out->records)
+        return fail(HF_EINVAL, "per-cut records come from the device-resident entry points only");
     cudaSetDevice(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
     while (true) {  // bounded wait: queued (batching) and then running
@@ -981,7 +1015,7 @@ namespace {
 
 struct BatchLayout {
     size_t off_dev, off_ch, off_plans, off_exec, off_stats, off_tpre, off_cnt, off_tctr, off_fb, off_bucket, off_rc,
-        off_pend_cnt, off_pend_rng, off_pend_sum, off_pend_comp, off_rc_reco, off_rc_pass, bytes;
+        off_pend_cnt, off_pend_rng, off_pend_sum, off_pend_comp, off_rc_reco, off_rc_f, off_maxf, off_rec_pre, bytes;
     size_t table_bytes;  // [off_dev, off_fb): uploaded from the host
     unsigned rc_cap;
 };
@@ -1062,6 +1096,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         b.O.cutflow = (unsigned long long*)k.out.cutflow;
         b.O.hist = (unsigned long long*)k.out.hist;
         b.O.rc_total = (unsigned long long*)k.out.recheck_count;
+        if (hf_status rs = records_out(*A, k.out, b.O)) return rs;
         if (!b.O.cutflow) fb_words += MAX_CUTS + 1;
         if (!b.O.hist) fb_words += MAX_BINS + 2;
         if (!b.O.rc_total) fb_words += 1;
@@ -1135,8 +1170,12 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     o += 16 * cap;
     L.off_rc_reco = o = align_up(o, 256);
     o += 16 * cap;
-    L.off_rc_pass = o = align_up(o, 256);
+    L.off_rc_f = o = align_up(o, 256);
     o += 4 * cap;
+    L.off_maxf = o = align_up(o, 256);
+    o += std::max<uint64_t>(ev_total, 1);
+    L.off_rec_pre = o = align_up(o, 256);
+    o += 8 * (blocks + 1);
     L.bytes = align_up(o, 256);
     // the small counter block of single runs (error word at SM_ERR) stays at the
     // arena's start, so that hf_device_error reads batches too
@@ -1153,6 +1192,10 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         if (!b.O.cutflow) { b.O.cutflow = fb; fb += MAX_CUTS + 1; }
         if (!b.O.hist) { b.O.hist = fb; fb += MAX_BINS + 2; }
         if (!b.O.rc_total) { b.O.rc_total = fb; fb += 1; }
+        if (b.O.rec) {
+            b.O.maxf = (uint8_t*)(dbase + L.off_maxf) + b.ev0;
+            BL.records = true;
+        }
     }
     BatchDev B;
     memset(&B, 0, sizeof B);
@@ -1168,6 +1211,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     B.n_semi0 = n_semi0;
     B.n_blocks = (uint32_t)blocks;
     B.n_plans = np;
+    B.rec_pre = (unsigned long long*)(dbase + L.off_rec_pre);
     {
         Scratch& S = B.S;
         char* sm = ctx->arena;  // small counter block of the arena
@@ -1182,7 +1226,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         S.pend_cnt = (unsigned*)(dbase + L.off_pend_cnt);
         S.pend_rng = (uint2*)(dbase + L.off_pend_rng);
         S.rc_reco = (float4*)(dbase + L.off_rc_reco);
-        S.rc_pass = (unsigned*)(dbase + L.off_rc_pass);
+        S.rc_f = (int*)(dbase + L.off_rc_f);
         S.pend_sum = (float4*)(dbase + L.off_pend_sum);
         S.pend_comp = (float4*)(dbase + L.off_pend_comp);
         S.stats = nullptr;
@@ -1221,8 +1265,8 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     // the launch sequence: replay the captured graph when it was captured for
     // the same arena, table layout, launch shape and scheduler states
     const BatchDev* Bd = (const BatchDev*)(dbase + L.off_dev);
-    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)Bd, (uint64_t)ctx->side.n, BL.semi_mask, BL.full_mask, BL.dilep,
-                                 BL.smem_dilep, np};
+    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)Bd, (uint64_t)ctx->side.n, BL.semi_mask, BL.full_mask,
+                                 BL.dilep, BL.records, BL.smem_dilep, np};
     for (int n = 0; n < NBUCKET; ++n) key.push_back(BL.smem_semi[n]);
     for (uint32_t p = 0; p < np; ++p) {
         Analysis* A = get_analysis(ctx, plan_ids[p]);

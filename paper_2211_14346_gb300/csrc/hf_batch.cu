@@ -60,7 +60,10 @@ __global__ void k_bzero(const BatchDev* __restrict__ Bp)
         if (threadIdx.x < 32) ch.cnt[threadIdx.x] = 0;
         if (threadIdx.x <= (unsigned)P.n_cuts) ch.O.cutflow[threadIdx.x] = 0;
         for (int b = threadIdx.x; b < P.nbins + 2; b += blockDim.x) ch.O.hist[b] = 0;
-        if (threadIdx.x == 0) *ch.O.rc_total = 0;
+        if (threadIdx.x == 0) {
+            *ch.O.rc_total = 0;
+            if (ch.O.rec) *ch.O.n_rec = 0;
+        }
     }
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n_plans * 3 * MAX_CUTS;
          i += gridDim.x * blockDim.x)
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(BLOCK1) k_bstage1(const BatchDev* __restrict__
                     loc = atomicAdd(&s_cnt[bucket], 1u);
                 } else {
                     atomicAdd(&s_fc[f1], (unsigned long long)ch.V);
-                    write_zero_event(ch.O, e);
+                    write_stage1_event(P, ch.C, ch.O, e, f1);
                 }
             }
         }
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(BLOCK) k_brecheck(const BatchDev* __restrict__
         atomicAdd(ch.O.rc_total, 1ull);
         if (f == P.n_cuts) atomicAdd(&ch.O.hist[bin], 1ull);
         S.rc_reco[i] = reco;
-        S.rc_pass[i] = f == P.n_cuts;
+        S.rc_f[i] = f;
     }
 }
 
@@ -205,11 +208,58 @@ __global__ void __launch_bounds__(BLOCK) k_bfinish(const BatchDev* __restrict__ 
     const unsigned n = *S.pend_count;
     const unsigned w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (unsigned s = w0; s < n; s += nw) {
+        // the slot's chunk (read by every lane: the plan sets n_cuts)
+        const BChunk& ch = B.ch[S.rc[S.pend_rng[s].x].chunk];
+        const Plan& P = B.plans[ch.plan];
         unsigned cnt;
         float4 sum, comp;
+        int maxf;
         RcEntry first;
-        finish_pending(S, s, cnt, sum, comp, first);
-        if ((threadIdx.x & 31u) == 0) write_event(B.ch[first.chunk].O, first.event, cnt, sum, comp);
+        finish_pending(S, P.n_cuts, s, cnt, sum, comp, maxf, first);
+        if ((threadIdx.x & 31u) == 0) {
+            write_event(ch.O, first.event, cnt, sum, comp);
+            if (ch.O.maxf) ch.O.maxf[first.event] = (uint8_t)max((int)ch.O.maxf[first.event], maxf);
+        }
+    }
+}
+
+// Per-cut records of every recording chunk (stage-1 blocks of BLOCK1 events;
+// see k_rec_count / k_rec_write).
+__global__ void __launch_bounds__(BLOCK1) k_brec_count(const BatchDev* __restrict__ Bp)
+{
+    const BatchDev& B = *Bp;
+    unsigned long long* pre = B.rec_pre;
+    for (unsigned blk = blockIdx.x; blk < B.n_blocks; blk += gridDim.x) {
+        const BChunk& ch = B.ch[chunk_of_block(B, blk)];
+        const uint32_t e = (blk - ch.blk0) * BLOCK1 + threadIdx.x;
+        const unsigned long long c = ch.O.rec && e < ch.n ? rec_count(B.plans[ch.plan], ch.O.maxf[e]) : 0u;
+        unsigned long long total;
+        block_excl_scan(c, &total);
+        if (threadIdx.x == 0) pre[blk] = total;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_brec_scan(const BatchDev* __restrict__ Bp)
+{
+    scan_blocks(Bp->rec_pre, Bp->n_blocks, nullptr);
+}
+
+__global__ void __launch_bounds__(BLOCK1) k_brec_write(const BatchDev* __restrict__ Bp)
+{
+    const BatchDev& B = *Bp;
+    const unsigned long long* pre = B.rec_pre;
+    for (unsigned blk = blockIdx.x; blk < B.n_blocks; blk += gridDim.x) {
+        const BChunk& ch = B.ch[chunk_of_block(B, blk)];
+        const Plan& P = B.plans[ch.plan];
+        const uint32_t e = (blk - ch.blk0) * BLOCK1 + threadIdx.x;
+        const int maxf = ch.O.rec && e < ch.n ? ch.O.maxf[e] : 0;
+        unsigned long long total;
+        const unsigned long long k = pre[blk] - pre[ch.blk0] + block_excl_scan(rec_count(P, maxf), &total);
+        if (ch.O.rec) {
+            if (e < ch.n) write_records(P, ch.C, ch.O, e, maxf, k);
+            if (blk == ch.blk0 && threadIdx.x == 0)
+                *ch.O.n_rec = pre[ch.blk0 + (ch.n + BLOCK1 - 1) / BLOCK1] - pre[ch.blk0];
+        }
     }
 }
 
@@ -262,6 +312,11 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
     }
     k_brecheck<<<L.sms * 4, BLOCK, 0, st>>>(B);
     k_bfinish<<<L.sms * 2, BLOCK, 0, st>>>(B);
+    if (L.records) {
+        k_brec_count<<<L.sms * 8, BLOCK1, 0, st>>>(B);
+        k_brec_scan<<<1, 1024, 0, st>>>(B);
+        k_brec_write<<<L.sms * 8, BLOCK1, 0, st>>>(B);
+    }
     return cudaGetLastError();
 }
 

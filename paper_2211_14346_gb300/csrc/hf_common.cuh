@@ -15,6 +15,93 @@ __device__ __forceinline__ void write_zero_event(const Out& O, uint32_t e)
     if (O.mask) O.mask[e] = 0;
     if (O.n_surv) O.n_surv[e] = 0;
     if (O.reco) O.reco[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (O.maxf) O.maxf[e] = 0;
+}
+
+// ------------------------------------------------------------------ per-cut records
+// Per-cut variable recording (Sect. 3: the variables the user chose are kept
+// at every selection level, at their default where not yet updated).  The
+// event paths store maxf, the most cuts (user order) passed by any variation
+// of the event; after the run, event e gets one record per recorded level
+// k < maxf, written in (event, level) order by k_rec_count / k_rec_scan /
+// k_rec_write.
+__device__ __forceinline__ unsigned rec_count(const Plan& P, int maxf)
+{
+    return __popc(P.rec_levels & (maxf >= 32 ? 0xffffffffu : ((1u << (maxf > 0 ? maxf : 0)) - 1u)));
+}
+
+// Writes event e's records at k, k+1, ... (r: its reconstructed means, the
+// values of the last level).  Records past rec_cap are not written.
+__device__ inline void write_records(const Plan& P, const Cols& C, const Out& O, uint32_t e, int maxf,
+                                     unsigned long long k)
+{
+    unsigned lv = P.rec_levels & (maxf >= 32 ? 0xffffffffu : ((1u << (maxf > 0 ? maxf : 0)) - 1u));
+    if (!lv) return;
+    float val[4];
+    const uint32_t n = C.jet_off[e + 1] - C.jet_off[e];
+    const float4 r = (lv >> (P.n_cuts - 1) & 1u) && O.reco ? O.reco[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < 4; ++i) {
+        const int var = P.rec_var[i];
+        float x = 0.f;
+        if (var == VAR_NJETS) {
+            x = (float)n;
+        } else if (var == VAR_NBTAG) {
+            x = (float)__popc(C.btag[e] & ((1u << n) - 1u));
+        } else if (var == VAR_LEP_PT) {
+            const float4 l = C.lep[P.model == MODEL_DILEP ? 2 * (uint64_t)e : (uint64_t)e];
+            x = (float)__dsqrt_rn((double)l.x * (double)l.x + (double)l.y * (double)l.y);
+        } else if (var == VAR_MET) {
+            const float2 m = C.met[e];
+            x = (float)__dsqrt_rn((double)m.x * (double)m.x + (double)m.y * (double)m.y);
+        }
+        val[i] = x;
+    }
+    for (; lv; lv &= lv - 1u, ++k) {
+        if (k >= O.rec_cap) return;
+        const int level = __ffs(lv) - 1;
+        Record rec;
+        rec.event = e;
+        rec.level = (uint32_t)level;
+        for (int i = 0; i < 4; ++i) {
+            const int var = P.rec_var[i];
+            float x = val[i];
+            if (var >= VAR_RECO0 && var < VAR_RECO0 + 4)
+                x = level == P.n_cuts - 1 ? (var == VAR_RECO0 ? r.x : var == VAR_RECO0 + 1 ? r.y
+                                             : var == VAR_RECO0 + 2 ? r.z : r.w) : 0.f;
+            rec.value[i] = x;
+        }
+        O.rec[k] = rec;
+    }
+}
+
+// Exclusive prefix sum over the threads of a block (blockDim.x a multiple of
+// 32, at most 1024); every thread calls.  Returns x's prefix and the total.
+__device__ inline unsigned long long block_excl_scan(unsigned long long x, unsigned long long* total)
+{
+    __shared__ unsigned long long s_w[32];
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (unsigned)o) inc += y;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = lane < nw ? s_w[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= (unsigned)o) t += y;
+        }
+        if (lane < nw) s_w[lane] = t;  // inclusive prefix of the warp totals
+    }
+    __syncthreads();
+    const unsigned long long before = w ? s_w[w - 1] : 0ull;
+    *total = s_w[nw - 1];
+    __syncthreads();
+    return before + inc - x;
 }
 
 // Exact decision of pT(x, y) > thr: FP32 with a rounding band, FP64 inside it.
@@ -329,6 +416,27 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
     return f;
 }
 
+// In place: pre[0..n) := exclusive prefix, pre[n] := total (also *total_out
+// when given).  One block of 1024 threads, each over a contiguous segment.
+__device__ inline void scan_blocks(unsigned long long* pre, unsigned n, unsigned long long* total_out)
+{
+    const unsigned seg = (n + blockDim.x - 1) / blockDim.x;
+    const unsigned lo = min(n, threadIdx.x * seg), hi = min(n, lo + seg);
+    unsigned long long sum = 0;
+    for (unsigned i = lo; i < hi; ++i) sum += pre[i];
+    unsigned long long total;
+    unsigned long long run = block_excl_scan(sum, &total);
+    for (unsigned i = lo; i < hi; ++i) {
+        const unsigned long long x = pre[i];
+        pre[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) {
+        pre[n] = total;
+        if (total_out) *total_out = total;
+    }
+}
+
 // ------------------------------------------------------------------ pending events
 // An event with flagged units keeps the compensated sum of its unflagged
 // survivors in a pending slot; its flagged units go to the recheck list,
@@ -350,6 +458,13 @@ __device__ __forceinline__ void write_event(const Out& O, uint32_t e, unsigned c
         }
         O.reco[e] = r;
     }
+}
+
+// Event e rejected by its stage-1 cuts: every variation passes cuts 0..f1-1.
+__device__ __forceinline__ void write_stage1_event(const Plan& P, const Cols& C, const Out& O, uint32_t e, int f1)
+{
+    write_zero_event(O, e);
+    if (O.maxf) O.maxf[e] = (uint8_t)f1;
 }
 
 __device__ __forceinline__ void acc4(float4& s, float4& c, float4 x)
@@ -441,6 +556,7 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
         int bin = 0;
         int f = unit_fp64(P, C, e, event_id, seed, vs[i], s1bits, &reco, &bin);
         atomicAdd(&fc[f], 1ull);
+        if (O.maxf) O.maxf[e] = (uint8_t)max((int)O.maxf[e], f);
         if (f == P.n_cuts) {
             ++cnt;
             atomicAdd(&hist[bin], 1u);
@@ -453,21 +569,25 @@ static __device__ __noinline__ void pend_event(const Plan& P, const Cols& C, con
 
 // Completion of pending slot s by one warp: the unflagged partial sum plus the
 // passing entries' FP64 results.  Lane 0 returns the totals and the event.
-__device__ __forceinline__ void finish_pending(const Scratch& S, unsigned s, unsigned& cnt, float4& sum, float4& comp,
-                                               RcEntry& first)
+__device__ __forceinline__ void finish_pending(const Scratch& S, int n_cuts, unsigned s, unsigned& cnt, float4& sum,
+                                               float4& comp, int& maxf, RcEntry& first)
 {
     const unsigned lane = threadIdx.x & 31u;
     const uint2 rg = S.pend_rng[s];
     sum = make_float4(0.f, 0.f, 0.f, 0.f);
     comp = sum;
     cnt = 0;
+    maxf = -1;
     for (unsigned i = lane; i < rg.y; i += 32) {
-        if (S.rc_pass[rg.x + i]) {
+        const int f = S.rc_f[rg.x + i];
+        maxf = max(maxf, f);
+        if (f == n_cuts) {
             ++cnt;
             acc4(sum, comp, S.rc_reco[rg.x + i]);
         }
     }
     warp_merge4(sum, comp, cnt);
+    maxf = __reduce_max_sync(0xffffffffu, maxf);
     if (lane == 0) {
         float4 ps = S.pend_sum[s], pc = S.pend_comp[s];
         merge4(ps, pc, sum, comp);
@@ -508,6 +628,23 @@ __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsi
     }
 }
 
+// Per-cut records: the most cuts passed by the event's unflagged units
+// (the rechecked ones are added when their event completes).  Out of line:
+// inlined into the tile epilogue, this never-taken path cost the stage-2
+// kernels about 1 % (measured).  warp: the calling warp shares the work.
+static __device__ __noinline__ void store_maxf(const int* uf, uint32_t V, uint8_t* dst, bool warp)
+{
+    int m = 0;
+    if (warp) {
+        for (uint32_t v = threadIdx.x & 31u; v < V; v += 32) m = max(m, uf[v]);
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31u) == 0) *dst = (uint8_t)m;
+    } else {
+        for (uint32_t v = 0; v < V; ++v) m = max(m, uf[v]);
+        *dst = (uint8_t)m;
+    }
+}
+
 // Per-event reduction of a tile's units: compensated sums of the surviving
 // units' reconstructed quantities; events without flagged units are written,
 // the others get a pending slot and their flagged units go to the recheck
@@ -538,6 +675,7 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
                     acc4(sum, comp, ureco[u]);
                 }
             }
+            if (O.maxf) store_maxf(uf + ev * (int)V, V, O.maxf + e, false);
             if (nflag == 0) write_event(O, e, cnt, sum, comp);
             else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
         }
@@ -552,7 +690,7 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
         unsigned cnt = 0, nflag = 0;
         for (uint32_t v0 = 0; v0 < V; v0 += 32) {
             const uint32_t v = v0 + lane;
-            const int f = v < V ? uf[u0 + (int)v] : 0;
+            const int f = v < V ? uf[u0 + (int)v] : -1;
             nflag += __popc(__ballot_sync(0xffffffffu, v < V && f < 0));
             if (v < V && f == P.n_cuts) {
                 ++cnt;
@@ -560,6 +698,7 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
             }
         }
         warp_merge4(sum, comp, cnt);
+        if (O.maxf) store_maxf(uf + u0, V, O.maxf + e, true);
         if (nflag == 0) {
             if (lane == 0) write_event(O, e, cnt, sum, comp);
             continue;
@@ -583,6 +722,7 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
         // list full: the lanes evaluate the flagged units in FP64
         float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = s2;
         unsigned n2 = 0;
+        int mf = 0;
         for (uint32_t v0 = 0; v0 < V; v0 += 32) {
             const uint32_t v = v0 + lane;
             if (v < V && uf[u0 + (int)v] < 0) {
@@ -590,6 +730,7 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
                 int bin = 0;
                 const int f2 = unit_fp64(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin);
                 atomicAdd(&fc[f2], 1ull);
+                mf = max(mf, f2);
                 if (f2 == P.n_cuts) {
                     ++n2;
                     atomicAdd(&hist[bin], 1u);
@@ -599,7 +740,9 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
         }
         __syncwarp();
         warp_merge4(s2, c2, n2);
+        mf = __reduce_max_sync(0xffffffffu, mf);
         if (lane == 0) {
+            if (O.maxf) O.maxf[e] = (uint8_t)max((int)O.maxf[e], mf);
             merge4(sum, comp, s2, c2);
             atomicAdd(O.rc_total, (unsigned long long)nflag);
             write_event(O, e, cnt + n2, sum, comp);

@@ -39,6 +39,9 @@ enum : int { PROF_UNITS = 0, PROF_EVENTS = 1, PROF_PAIRINGS = 2, PROF_CANDS = 3,
 // Error word bits (device -> host).
 enum : unsigned { ERR_COLUMNS = 1u, ERR_RECHECK_FULL = 2u };
 
+// Variables of the per-cut recording (values of HF_VAR_*).
+enum : int { VAR_NONE = 0, VAR_NJETS = 1, VAR_NBTAG = 2, VAR_LEP_PT = 3, VAR_MET = 4, VAR_RECO0 = 5 };
+
 // Everything a kernel needs to know about an analysis.  Passed by value.
 struct Plan {
     int model;
@@ -67,6 +70,8 @@ struct Plan {
     double dmW, dmt, dsigma_t, dsigma_W, dmH, dsigma_jet, dsigma_met;
     double dp0[MAX_CUTS], dp1[MAX_CUTS];
     double dlo, dhi;
+    unsigned rec_levels; // per-cut recording: bit k records events passing cuts 0..k
+    int rec_var[4];      // HF_VAR_* of each recorded value
 };
 
 struct Cols {
@@ -79,6 +84,13 @@ struct Cols {
     uint64_t n_jets_total;
 };
 
+// One per-cut record (the layout of hf_record).
+struct Record {
+    uint32_t event;
+    uint32_t level;
+    float value[4];
+};
+
 struct Out {
     uint8_t* mask;
     uint16_t* n_surv;
@@ -86,6 +98,10 @@ struct Out {
     unsigned long long* cutflow;  // n_cuts + 1, device accumulators (zeroed per run)
     unsigned long long* hist;     // nbins + 2
     unsigned long long* rc_total; // units rechecked in FP64
+    Record* rec;                  // per-cut records (null: none)
+    unsigned long long rec_cap;
+    unsigned long long* n_rec;    // records produced
+    uint8_t* maxf;                // [N] scratch of a recording run: most cuts passed by a variation
 };
 
 // Recheck list entry: one unit whose FP32 evaluation came within an error
@@ -109,8 +125,9 @@ struct Scratch {
     RcEntry* rc;          // [rc_cap] flagged units; those of one event are contiguous, in variation order
     unsigned rc_cap;
     float4* rc_reco;      // [rc_cap] FP64 result of entry i: reconstructed quantities
-    unsigned* rc_pass;    // [rc_cap] FP64 result of entry i: 1 if the unit passes every cut
+    int* rc_f;            // [rc_cap] FP64 result of entry i: cuts passed in user order
     unsigned* pend_cnt;   // [rc_cap] surviving unflagged units of pending event s
+    unsigned long long* rec_pre; // [stage-1 blocks + 1] records per block, then their exclusive prefix
     uint2* pend_rng;      // [rc_cap] (first entry, number of entries) of pending event s
     float4* pend_sum;     // [rc_cap] compensated sum over the unflagged survivors
     float4* pend_comp;    // [rc_cap] its compensation terms
@@ -156,6 +173,7 @@ struct BatchDev {
     uint32_t n_semi0;             // of which [0, n_semi0) without and [n_semi0, n_semi) with the full fit
     uint32_t n_blocks;            // stage-1 blocks of the batch
     uint32_t n_plans;
+    unsigned long long* rec_pre;  // [n_blocks + 1] per-cut records per stage-1 block, then their prefix
     Scratch S;                    // recheck list, pending slots, error word of the batch
 };
 

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_stage1(const Plan P, const Cols C, uint
                 loc = atomicAdd(&s_cnt[bucket], 1u);
             } else {
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
-                write_zero_event(O, e);
+                write_stage1_event(P, C, O, e, f1);
             }
         }
     }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
         atomicAdd(&s_fc[f], 1ull);
         if (f == P.n_cuts) atomicAdd(&s_hist[bin], 1u);
         S.rc_reco[i] = reco;
-        S.rc_pass[i] = f == P.n_cuts;
+        S.rc_f[i] = f;
     }
     if (mine) atomicAdd(O.rc_total, mine);
     __syncthreads();
@@ -116,18 +116,49 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
     flush_hist(P, O, s_hist);
 }
 
+// ------------------------------------------------------------------ per-cut records
+// Records per block of events (blockDim.x events from blockIdx.x).
+__global__ void __launch_bounds__(256) k_rec_count(const Plan P, const Out O, uint32_t N, unsigned long long* pre)
+{
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long c = e < N ? rec_count(P, O.maxf[e]) : 0u;
+    unsigned long long total;
+    block_excl_scan(c, &total);
+    if (threadIdx.x == 0) pre[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_rec_scan(unsigned long long* pre, unsigned n,
+                                                   unsigned long long* total_out)
+{
+    scan_blocks(pre, n, total_out);
+}
+
+__global__ void __launch_bounds__(256) k_rec_write(const Plan P, const Cols C, const Out O, uint32_t N,
+                                                   const unsigned long long* pre)
+{
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int maxf = e < N ? O.maxf[e] : 0;
+    unsigned long long total;
+    const unsigned long long k = pre[blockIdx.x] + block_excl_scan(rec_count(P, maxf), &total);
+    if (e < N) write_records(P, C, O, e, maxf, k);
+}
+
 // ------------------------------------------------------------------ k_finish
 // Completion of the pending events after the recheck, one warp per slot.
-__global__ void __launch_bounds__(BLOCK) k_finish(const Out O, Scratch S)
+__global__ void __launch_bounds__(BLOCK) k_finish(const Plan P, const Cols C, const Out O, Scratch S)
 {
     const unsigned n = *S.pend_count;
     const unsigned w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (unsigned s = w0; s < n; s += nw) {
         unsigned cnt;
         float4 sum, comp;
+        int maxf;
         RcEntry first;
-        finish_pending(S, s, cnt, sum, comp, first);
-        if ((threadIdx.x & 31u) == 0) write_event(O, first.event, cnt, sum, comp);
+        finish_pending(S, P.n_cuts, s, cnt, sum, comp, maxf, first);
+        if ((threadIdx.x & 31u) == 0) {
+            write_event(O, first.event, cnt, sum, comp);
+            if (O.maxf) O.maxf[first.event] = (uint8_t)max((int)O.maxf[first.event], maxf);
+        }
     }
 }
 
@@ -204,7 +235,12 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
         if (ev) cudaEventRecord(ev[2], st);
     }
     k_recheck<<<sms * 4, BLOCK, 0, st>>>(P, C, O, S, seed, first_id);
-    k_finish<<<sms * 2, BLOCK, 0, st>>>(O, S);
+    k_finish<<<sms * 2, BLOCK, 0, st>>>(P, C, O, S);
+    if (O.rec) {
+        k_rec_count<<<nb, 256, 0, st>>>(P, O, N, S.rec_pre);
+        k_rec_scan<<<1, 1024, 0, st>>>(S.rec_pre, nb, O.n_rec);
+        k_rec_write<<<nb, 256, 0, st>>>(P, C, O, N, S.rec_pre);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
 }

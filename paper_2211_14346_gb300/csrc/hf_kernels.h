@@ -44,6 +44,7 @@ struct SideStreams {
     cudaEvent_t join[MAX_SIDE];
 };
 
+
 cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, const Out& O, const Scratch& S,
                        uint64_t seed, uint64_t first_id, bool plain, int sms, cudaStream_t st,
                        cudaEvent_t* ev = nullptr, const SideStreams* side = nullptr, int upt = 0);
@@ -56,6 +57,7 @@ struct BatchLaunch {
     size_t smem_semi[NBUCKET];     // dynamic shared memory of the multiplicity-n kernels
     bool dilep;                    // the batch has dilepton chunks
     size_t smem_dilep;
+    bool records;                  // some chunk records per-cut variables
 };
 typedef cudaError_t (*BS2Launcher)(const BatchDev*, size_t, int, cudaStream_t);
 template <int N, bool F>

@@ -29,13 +29,15 @@ constexpr unsigned NA_RC_CAP = 1u << 16;  // recheck entries; more are evaluated
 constexpr size_t NA_SMALL = 0;                                      // counters, 256 B
 constexpr size_t NA_BUCKET = 256;                                   // uint2[NA_MAX_EVENTS]
 constexpr size_t NA_RC = NA_BUCKET + 8 * NA_MAX_EVENTS;             // RcEntry[NA_RC_CAP]
-constexpr size_t NA_PEND_CNT = NA_RC + 16 * (size_t)NA_RC_CAP;      // unsigned[NA_RC_CAP]
+constexpr size_t NA_PEND_CNT = NA_RC + 16 * (size_t)NA_RC_CAP;      // int[NA_RC_CAP]
 constexpr size_t NA_PEND_RNG = NA_PEND_CNT + 4 * (size_t)NA_RC_CAP;   // uint2[NA_RC_CAP]
 constexpr size_t NA_PEND_SUM = NA_PEND_RNG + 8 * (size_t)NA_RC_CAP;   // float4[NA_RC_CAP]
 constexpr size_t NA_PEND_COMP = NA_PEND_SUM + 16 * (size_t)NA_RC_CAP;
 constexpr size_t NA_RC_RECO = NA_PEND_COMP + 16 * (size_t)NA_RC_CAP;  // float4[NA_RC_CAP]
-constexpr size_t NA_RC_PASS = NA_RC_RECO + 16 * (size_t)NA_RC_CAP;    // unsigned[NA_RC_CAP]
-constexpr size_t NA_CUTFLOW = NA_RC_PASS + 4 * (size_t)NA_RC_CAP;     // u64[MAX_CUTS+1]
+constexpr size_t NA_RC_F = NA_RC_RECO + 16 * (size_t)NA_RC_CAP;       // int[NA_RC_CAP]
+constexpr size_t NA_MAXF = NA_RC_F + 4 * (size_t)NA_RC_CAP;           // u8[NA_MAX_EVENTS]
+constexpr size_t NA_REC_PRE = NA_MAXF + NA_MAX_EVENTS;                 // u64[NA_MAX_EVENTS/256 + 1]
+constexpr size_t NA_CUTFLOW = NA_REC_PRE + 8 * (NA_MAX_EVENTS / 256) + 256;  // u64[MAX_CUTS+1]
 constexpr size_t NA_HIST = NA_CUTFLOW + 256;                          // u64[MAX_BINS+2]
 constexpr size_t NA_RCTOT = NA_HIST + 8 * (MAX_BINS + 2 + 30);        // u64
 constexpr size_t NA_BYTES = NA_RCTOT + 256;
@@ -116,7 +118,8 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
     S.pend_cnt = (unsigned*)(base + NA_PEND_CNT);
     S.pend_rng = (uint2*)(base + NA_PEND_RNG);
     S.rc_reco = (float4*)(base + NA_RC_RECO);
-    S.rc_pass = (unsigned*)(base + NA_RC_PASS);
+    S.rc_f = (int*)(base + NA_RC_F);
+    S.rec_pre = (unsigned long long*)(base + NA_REC_PRE);
     S.pend_sum = (float4*)(base + NA_PEND_SUM);
     S.pend_comp = (float4*)(base + NA_PEND_COMP);
     S.stats = nullptr;  // no scheduler: user order
@@ -133,6 +136,17 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
         O.cutflow = (unsigned long long*)dev_out->cutflow;
         O.hist = (unsigned long long*)dev_out->hist;
         O.rc_total = (unsigned long long*)dev_out->recheck_count;
+        if (dev_out->records && P.rec_levels) {
+            if (!dev_out->n_records || ((uintptr_t)dev_out->records & 3))
+                return set_error(HF_EINVAL, "records need n_records and 4-byte alignment");
+            for (int i = 0; i < 4; ++i)
+                if (P.rec_var[i] >= VAR_RECO0 && !dev_out->reco)
+                    return set_error(HF_EINVAL, "recording a reconstructed quantity needs the reco output");
+            O.rec = (Record*)dev_out->records;
+            O.rec_cap = dev_out->record_cap;
+            O.n_rec = (unsigned long long*)dev_out->n_records;
+            O.maxf = (uint8_t*)(base + NA_MAXF);
+        }
     }
     if (!O.cutflow) O.cutflow = (unsigned long long*)(base + NA_CUTFLOW);
     if (!O.hist) O.hist = (unsigned long long*)(base + NA_HIST);
@@ -142,7 +156,8 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
     if ((e = cudaMemsetAsync(base + NA_SMALL, 0, 256, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(O.cutflow, 0, 8 * (P.n_cuts + 1), st)) != cudaSuccess ||
         (e = cudaMemsetAsync(O.hist, 0, 8 * (P.nbins + 2), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(O.rc_total, 0, 8, st)) != cudaSuccess)
+        (e = cudaMemsetAsync(O.rc_total, 0, 8, st)) != cudaSuccess ||
+        (O.rec && (e = cudaMemsetAsync(O.n_rec, 0, 8, st)) != cudaSuccess))
         return set_cuda_error(e, "cudaMemsetAsync(scratch)");
     if (n_events == 0) return HF_OK;
 

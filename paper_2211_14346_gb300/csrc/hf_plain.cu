@@ -38,7 +38,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
     se.event_id = first_id + e;
     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
     unsigned cnt = 0;
-    int nflag = 0;
+    int nflag = 0, maxf = -1;
     uint16_t vs[64];
     for (uint32_t v = 0; v < V; ++v) {
         UnitOut r = semi_unit_f<N, F>(P, P.exec2, P.n_exec2, se, v, seed);
@@ -54,6 +54,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
             r.bin = bin;
             atomicAdd(O.rc_total, 1ull);
         }
+        maxf = max(maxf, r.f);
         atomicAdd(&fc[r.f], 1ull);
         if (r.f == P.n_cuts) {
             ++cnt;
@@ -61,6 +62,7 @@ __device__ __noinline__ void plain_semi_event(const Plan& P, const Cols& C, cons
             acc4(sum, comp, r.reco);
         }
     }
+    if (O.maxf) O.maxf[e] = (uint8_t)max(maxf, 0);
     if (nflag == 0) write_event(O, e, cnt, sum, comp);
     else pend_event(P, C, O, S, e, first_id + e, seed, bits, cnt, sum, comp, vs, nflag, fc, hist);
 }
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain(const Plan P, const Cols C, uin
             int f1 = first_fail_stage1(P, bits);
             if (!needs_stage2(P, f1)) {
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
-                write_zero_event(O, e);
+                write_stage1_event(P, C, O, e, f1);
             } else {
                 if (P.has_full)
                     plain_dispatch<MAX_JETS, true>((int)n, P, C, O, S, e, V, seed, first_id, bits, s_fc, s_hist);

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain_dilep(const Plan P, const Cols 
             int f1 = first_fail_stage1(P, bits);
             if (!needs_stage2(P, f1)) {
                 atomicAdd(&s_fc[f1], (unsigned long long)V);
-                write_zero_event(O, e);
+                write_stage1_event(P, C, O, e, f1);
             } else {
                 const float4* jet = C.jets + a;
                 const float4 l1 = C.lep[2 * (uint64_t)e], l2 = C.lep[2 * (uint64_t)e + 1];
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain_dilep(const Plan P, const Cols 
                 const unsigned btag = C.btag[e];
                 float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
                 unsigned cnt = 0;
-                int nflag = 0;
+                int nflag = 0, maxf = -1;
                 uint16_t vs[64];
                 for (uint32_t v = 0; v < V; ++v) {
                     UnitOut r = dilep_unit_f(P, s_exec, P.n_exec2, jet, (int)n, btag, l1, l2, met, bits, first_id + e, v, seed);
@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain_dilep(const Plan P, const Cols 
                         r.bin = bin;
                         atomicAdd(O.rc_total, 1ull);
                     }
+                    maxf = max(maxf, r.f);
                     atomicAdd(&s_fc[r.f], 1ull);
                     if (r.f == P.n_cuts) {
                         ++cnt;
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(BLOCK) k_plain_dilep(const Plan P, const Cols 
                         acc4(sum, comp, r.reco);
                     }
                 }
+                if (O.maxf) O.maxf[e] = (uint8_t)max(maxf, 0);
                 if (nflag == 0) write_event(O, e, cnt, sum, comp);
                 else pend_event(P, C, O, S, e, first_id + e, seed, bits, cnt, sum, comp, vs, nflag, s_fc, s_hist);
             }

@@ -49,3 +49,28 @@ def max_rel_err(g, o):
     if not sel.any():
         return 0.0
     return float(np.max(np.abs(g[sel] - o[sel]) / np.abs(o[sel])))
+
+
+def assert_records(g, o, an, *, what=""):
+    """Per-cut records: same (event, level) pairs; measured variables
+    bit-equal (both sides round the same FP64 value to float); reconstructed
+    means within RTOL of the oracle's, as in assert_reco."""
+    names = list(an["record"].get("vars", ()))
+    names += ["none"] * (4 - len(names))
+    assert g.shape[0] == o["event"].shape[0], "%s: %d records, oracle %d" % (what, g.shape[0], o["event"].shape[0])
+    assert np.array_equal(g["event"], o["event"]), "%s: record events differ" % what
+    assert np.array_equal(g["level"], o["level"]), "%s: record levels differ" % what
+    oabs = o["run"]["reco_abs"]
+    for i, name in enumerate(names):
+        gv = g["value"][:, i].astype(np.float64)
+        ov = o["value"][:, i]
+        if name.startswith("reco"):
+            k = int(name[4])
+            scale = np.maximum(oabs[o["event"], k], np.abs(ov))
+            if an["model"] == "semilep" and k == 2:
+                scale = oabs[o["event"], 2] + oabs[o["event"], 3]
+            bad = np.nonzero(np.abs(gv - ov) > RTOL * scale)[0]
+        else:
+            bad = np.nonzero(g["value"][:, i] != ov.astype(np.float32))[0]
+        assert bad.size == 0, "%s: value %d (%s) differs at records %s: gpu %s orc %s" % (
+            what, i, name, bad[:5], gv[bad[:5]], ov[bad[:5]])

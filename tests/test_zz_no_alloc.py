@@ -21,17 +21,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _desc(an):
-    from paper_2211_14346_gb300 import _lib, _cut_struct, _f32
-    cuts = _cut_struct(an["cuts"])
-    d = _lib.hf_analysis_desc()
-    d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
-    d.n_cuts = len(an["cuts"])
-    d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
-    for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
-        setattr(d, k, _f32(an[k]))
-    nb, lo, hi = an["hist"]
-    d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
-    return d, cuts
+    from paper_2211_14346_gb300 import analysis_desc
+    return analysis_desc(an)
 
 
 def test_noalloc_matches_run_device_twice():
