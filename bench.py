@@ -53,13 +53,14 @@ def _args():
     p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
     p.add_argument("--rates", default="0.5,0.9,1.2", help="served: arrival rates as fractions of measured capacity")
     p.add_argument("--workload", default="semilep16",
-                   choices=["semilep16", "batched", "served", "dilep", "unsmeared", "fullfit", "tthsci"],
+                   choices=["semilep16", "batched", "served", "dilep", "unsmeared", "fullfit", "tthsci", "records"],
                    help="semilep16: the headline (10M semileptonic events x 16 variations); "
                         "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs; "
                         "served: open-loop requests with continuous batching; dilep: 2M ttH-like dilepton events x 64; "
                         "unsmeared: 10M semileptonic events, no smearing (the column-scan chain); "
                         "fullfit: 2M semileptonic events x 16 with the full Eq. 1 fit; "
-                        "tthsci: 20k dilepton events x 1024 variations of a 1 %% resolution (the ttH_sci shape)")
+                        "tthsci: 20k dilepton events x 1024 variations of a 1 %% resolution (the ttH_sci shape); "
+                        "records: the headline with per-cut variable recording at every level")
     p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
     p.add_argument("--max-chunk", type=int, default=100000, help="batched: largest chunk (log-uniform from 1000)")
     return p.parse_args()
@@ -578,7 +579,9 @@ def run_single_workload(a):
     the full Eq. 1 fit (both tops, both W bosons) as the last cut; tthsci:
     20,000 dilepton events x 1024 variations of a 1 % jet-energy resolution
     and a 1 GeV MET resolution (the paper's ttH_sci pseudo-experiments, Sect.
-    4; data seed 3, Philox seed 1004).  Device-resident columns; the plain
+    4; data seed 3, Philox seed 1004); records: the headline configuration
+    with per-cut variable recording at all six levels (four variables), timed
+    beside the same run without recording.  Device-resident columns; the plain
     one-thread-per-event form timed beside it on the same data."""
     import numpy as np
     import torch
@@ -593,6 +596,11 @@ def run_single_workload(a):
     elif a.workload == "tthsci":
         N = a.events if a.events != N_EVENTS else 20_000
         cols, an, Vw, seed, name = synth.gen_dilep(N, 3), analyses.tth_sci(), 1024, 1004, "dilep_tthsci_20k_x1024"
+    elif a.workload == "records":
+        N = a.events
+        an = analyses.config2()
+        an["record"] = dict(levels=list(range(len(an["cuts"]))), vars=["njets", "lep_pt", "met", "reco0"])
+        cols, Vw, seed, name = synth.gen_semilep(N, DATA_SEED), V, SMEAR_SEED, "semilep_smeared_10M_x16_records"
     elif a.workload == "fullfit":
         N = a.events if a.events != N_EVENTS else 2_000_000
         cols, an, Vw, seed, name = (synth.gen_semilep(N, DATA_SEED), analyses.semilep_full(0.10, 10.0), V, SMEAR_SEED,
@@ -641,6 +649,26 @@ def run_single_workload(a):
                              ms_recheck=prof["ms_recheck"] / runs, pairings=prof["pairings_dilep"] // runs),
                 plain=dict(value=N / (ms_plain / 1e3), ms_per_step=ms_plain), speedup_vs_plain=ms_plain / ms,
                 clocks=clocks)
+    if a.workload == "records":
+        # the same run without recording, on the same data and tiles
+        an0 = dict(an)
+        an0.pop("record")
+        aid0 = eng.define(an0)
+        out0 = eng.results_for(aid0, N)
+        for _ in range(a.warmup):
+            eng.run_device(aid0, dc, V=Vw, seed=seed, out=out0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            eng.run_device(aid0, dc, V=Vw, seed=seed, out=out0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms0 = e0.elapsed_time(e1) / a.steps
+        line["records"] = dict(records_per_step=int(res["n_records"]), record_bytes_per_step=24 * int(res["n_records"]),
+                               ms_per_step_without=ms0, overhead=ms / ms0 - 1.0,
+                               levels=an["record"]["levels"], vars=an["record"]["vars"])
     if a.workload == "unsmeared":
         # algorithmic bytes of the chain: each cut reads the columns it needs for the
         # events that reach it (jet_off 4 B, b-tags 2 B, lepton pT 8 B, MET 8 B,
@@ -665,7 +693,7 @@ def main():
         run_batched(a)
     elif a.workload == "served":
         run_served(a)
-    elif a.workload in ("dilep", "unsmeared", "fullfit", "tthsci"):
+    elif a.workload in ("dilep", "unsmeared", "fullfit", "tthsci", "records"):
         run_single_workload(a)
     else:
         run_ours(a)
