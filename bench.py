@@ -282,9 +282,12 @@ def run_ours(a):
         fields = ("mask", "cutflow", "hist")
         host_out = dict(mask=np.zeros(N, np.uint8), cutflow=np.zeros(len(an["cuts"]) + 1, np.uint64),
                         hist=np.zeros(an["hist"][0] + 2, np.uint64))
-        for _ in range(1):
-            t0 = eng.submit(aid, hc, V=V, seed=SMEAR_SEED, first_event_id=first_id)
-            eng.fetch(aid, t0, N, fields=fields, out=host_out)
+        # warm-up with two chunks in flight, as in the timed loop (the memory
+        # pool grows to hold both before the clock starts)
+        for _ in range(2):
+            w = [eng.submit(aid, hc, V=V, seed=SMEAR_SEED, first_event_id=first_id) for _ in range(2)]
+            for t in w:
+                eng.fetch(aid, t, N, fields=fields, out=host_out)
         barrier()
         t_start = time.perf_counter()
         tickets = []

@@ -252,14 +252,11 @@ __global__ void __launch_bounds__(BLOCK1) k_brec_write(const BatchDev* __restric
         const BChunk& ch = B.ch[chunk_of_block(B, blk)];
         const Plan& P = B.plans[ch.plan];
         const uint32_t e = (blk - ch.blk0) * BLOCK1 + threadIdx.x;
-        const int maxf = ch.O.rec && e < ch.n ? ch.O.maxf[e] : 0;
-        unsigned long long total;
-        const unsigned long long k = pre[blk] - pre[ch.blk0] + block_excl_scan(rec_count(P, maxf), &total);
-        if (ch.O.rec) {
-            if (e < ch.n) write_records(P, ch.C, ch.O, e, maxf, k);
-            if (blk == ch.blk0 && threadIdx.x == 0)
-                *ch.O.n_rec = pre[ch.blk0 + (ch.n + BLOCK1 - 1) / BLOCK1] - pre[ch.blk0];
-        }
+        if (!ch.O.rec) continue;  // uniform over the block
+        const int maxf = e < ch.n ? ch.O.maxf[e] : 0;
+        write_block_records(P, ch.C, ch.O, e, e < ch.n, maxf, pre[blk] - pre[ch.blk0]);
+        if (blk == ch.blk0 && threadIdx.x == 0)
+            *ch.O.n_rec = pre[ch.blk0 + (ch.n + BLOCK1 - 1) / BLOCK1] - pre[ch.blk0];
     }
 }
 
@@ -311,7 +308,7 @@ cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t s
         }
     }
     k_brecheck<<<L.sms * 4, BLOCK, 0, st>>>(B);
-    k_bfinish<<<L.sms * 2, BLOCK, 0, st>>>(B);
+    k_bfinish<<<L.sms * 16, BLOCK, 0, st>>>(B);
     if (L.records) {
         k_brec_count<<<L.sms * 8, BLOCK1, 0, st>>>(B);
         k_brec_scan<<<1, 1024, 0, st>>>(B);

@@ -30,16 +30,11 @@ __device__ __forceinline__ unsigned rec_count(const Plan& P, int maxf)
     return __popc(P.rec_levels & (maxf >= 32 ? 0xffffffffu : ((1u << (maxf > 0 ? maxf : 0)) - 1u)));
 }
 
-// Writes event e's records at k, k+1, ... (r: its reconstructed means, the
-// values of the last level).  Records past rec_cap are not written.
-__device__ inline void write_records(const Plan& P, const Cols& C, const Out& O, uint32_t e, int maxf,
-                                     unsigned long long k)
+// Values of event e's records at level `level` (r: its reconstructed means).
+__device__ __forceinline__ void record_values(const Plan& P, const Cols& C, uint32_t e, float4 r, int level,
+                                              float* val)
 {
-    unsigned lv = P.rec_levels & (maxf >= 32 ? 0xffffffffu : ((1u << (maxf > 0 ? maxf : 0)) - 1u));
-    if (!lv) return;
-    float val[4];
     const uint32_t n = C.jet_off[e + 1] - C.jet_off[e];
-    const float4 r = (lv >> (P.n_cuts - 1) & 1u) && O.reco ? O.reco[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = 0; i < 4; ++i) {
         const int var = P.rec_var[i];
         float x = 0.f;
@@ -53,24 +48,10 @@ __device__ inline void write_records(const Plan& P, const Cols& C, const Out& O,
         } else if (var == VAR_MET) {
             const float2 m = C.met[e];
             x = (float)__dsqrt_rn((double)m.x * (double)m.x + (double)m.y * (double)m.y);
+        } else if (var >= VAR_RECO0 && var < VAR_RECO0 + 4 && level == P.n_cuts - 1) {
+            x = var == VAR_RECO0 ? r.x : var == VAR_RECO0 + 1 ? r.y : var == VAR_RECO0 + 2 ? r.z : r.w;
         }
         val[i] = x;
-    }
-    for (; lv; lv &= lv - 1u, ++k) {
-        if (k >= O.rec_cap) return;
-        const int level = __ffs(lv) - 1;
-        Record rec;
-        rec.event = e;
-        rec.level = (uint32_t)level;
-        for (int i = 0; i < 4; ++i) {
-            const int var = P.rec_var[i];
-            float x = val[i];
-            if (var >= VAR_RECO0 && var < VAR_RECO0 + 4)
-                x = level == P.n_cuts - 1 ? (var == VAR_RECO0 ? r.x : var == VAR_RECO0 + 1 ? r.y
-                                             : var == VAR_RECO0 + 2 ? r.z : r.w) : 0.f;
-            rec.value[i] = x;
-        }
-        O.rec[k] = rec;
     }
 }
 
@@ -414,6 +395,55 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         *reco = make_float4((float)mtop, (float)mw, (float)pz, (float)met);
     }
     return f;
+}
+
+// The records of one block of events (thread = event e, valid if `has`),
+// written from `base` on in (event, level) order.  They are assembled in
+// shared memory, REC_STAGE at a time, and copied out as consecutive 32-bit
+// words, so that a warp's stores cover whole sectors.  Every thread calls.
+constexpr int REC_STAGE = 1536;  // records per round (36 KB)
+
+__device__ inline void write_block_records(const Plan& P, const Cols& C, const Out& O, uint32_t e, bool has,
+                                           int maxf, unsigned long long base)
+{
+    __shared__ uint32_t s_rec[REC_STAGE * 6];
+    const unsigned cnt = has ? rec_count(P, maxf) : 0u;
+    unsigned long long total;
+    const unsigned long long excl = block_excl_scan(cnt, &total);
+    float vals[4];
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned lv = 0;
+    if (cnt) {
+        lv = P.rec_levels & (maxf >= 32 ? 0xffffffffu : ((1u << maxf) - 1u));
+        if ((lv >> (P.n_cuts - 1) & 1u) && O.reco) r = O.reco[e];
+        record_values(P, C, e, r, 0, vals);
+    }
+    for (unsigned long long r0 = 0; r0 < total; r0 += REC_STAGE) {
+        unsigned long long j = excl;
+        for (unsigned bits = lv; bits; bits &= bits - 1u, ++j) {
+            if (j < r0 || j >= r0 + REC_STAGE) continue;
+            const int level = __ffs(bits) - 1;
+            uint32_t* w = s_rec + (j - r0) * 6;
+            w[0] = e;
+            w[1] = (uint32_t)level;
+            for (int i = 0; i < 4; ++i) {
+                const int var = P.rec_var[i];
+                float x = vals[i];
+                if (var >= VAR_RECO0 && var < VAR_RECO0 + 4 && level != P.n_cuts - 1) x = 0.f;
+                if (var >= VAR_RECO0 && var < VAR_RECO0 + 4 && level == P.n_cuts - 1)
+                    x = var == VAR_RECO0 ? r.x : var == VAR_RECO0 + 1 ? r.y : var == VAR_RECO0 + 2 ? r.z : r.w;
+                w[2 + i] = __float_as_uint(x);
+            }
+        }
+        __syncthreads();
+        const unsigned long long nr = min((unsigned long long)REC_STAGE, total - r0);
+        const unsigned long long k0 = base + r0;
+        unsigned long long nw = 0;
+        if (k0 < O.rec_cap) nw = 6ull * min(nr, O.rec_cap - k0);
+        uint32_t* dst = (uint32_t*)O.rec + 6ull * k0;
+        for (unsigned long long i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = s_rec[i];
+        __syncthreads();
+    }
 }
 
 // In place: pre[0..n) := exclusive prefix, pre[n] := total (also *total_out

@@ -138,9 +138,7 @@ __global__ void __launch_bounds__(256) k_rec_write(const Plan P, const Cols C, c
 {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     const int maxf = e < N ? O.maxf[e] : 0;
-    unsigned long long total;
-    const unsigned long long k = pre[blockIdx.x] + block_excl_scan(rec_count(P, maxf), &total);
-    if (e < N) write_records(P, C, O, e, maxf, k);
+    write_block_records(P, C, O, e, e < N, maxf, pre[blockIdx.x]);
 }
 
 // ------------------------------------------------------------------ k_finish
@@ -235,7 +233,7 @@ cudaError_t launch_run(const Plan& P, const Cols& C, uint32_t N, uint32_t V, con
         if (ev) cudaEventRecord(ev[2], st);
     }
     k_recheck<<<sms * 4, BLOCK, 0, st>>>(P, C, O, S, seed, first_id);
-    k_finish<<<sms * 2, BLOCK, 0, st>>>(P, C, O, S);
+    k_finish<<<sms * 16, BLOCK, 0, st>>>(P, C, O, S);
     if (O.rec) {
         k_rec_count<<<nb, 256, 0, st>>>(P, O, N, S.rec_pre);
         k_rec_scan<<<1, 1024, 0, st>>>(S.rec_pre, nb, O.n_rec);
