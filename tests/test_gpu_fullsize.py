@@ -143,3 +143,42 @@ def test_fullfit_2M_x16(eng, orc):
     g = _run(eng, an, cols, V=V, seed=seed, tune_events=200_000)
     _properties(g, N, V, 0.002)
     _sampled(orc, an, cols, g, V=V, seed=seed, blocks=6, size=48, model="semilep", rng_seed=15)
+
+
+def test_records_10M_x16_all_levels(eng, orc):
+    """The records workload of bench.py: the headline with per-cut recording
+    at every level.  Whole chunk: records in (event, level) order, the last
+    level's events are the mask's, every recorded event also appears at each
+    lower recorded level, and the first level's variables are the columns'.
+    Sampled blocks of events: records equal to the oracle's."""
+    from paper_2211_14346_gb300 import DeviceColumns
+    from tests.parity import assert_records
+    N, V, seed = 10_000_000, 16, 1002
+    cols = _semilep_10M()
+    an = analyses.config2()
+    nc = len(an["cuts"])
+    an["record"] = dict(levels=list(range(nc)), vars=["njets", "lep_pt", "met", "reco0"])
+    aid = eng.define(an)
+    dc = DeviceColumns(cols)
+    eng.autotune(aid, dc.slice(0, 1_000_000), V=V, seed=seed)
+    g = eng.run_device(aid, dc, V=V, seed=seed).numpy()
+    assert eng.device_error() == 0
+    rec = g["records"]
+    assert g["n_records"] == len(rec)
+    key = rec["event"].astype(np.int64) * 64 + rec["level"]
+    assert np.all(np.diff(key) > 0)
+    per_level = np.bincount(rec["level"].astype(np.int64), minlength=nc)
+    assert np.all(np.diff(per_level) <= 0)
+    assert np.array_equal(rec["event"][rec["level"] == nc - 1], np.nonzero(g["mask"])[0])
+    lv0 = rec[rec["level"] == 0]
+    n = np.diff(cols.jet_off.astype(np.int64))
+    assert np.array_equal(lv0["value"][:, 0], n[lv0["event"]].astype(np.float32))
+    rng = np.random.default_rng(16)
+    for lo in rng.integers(0, N - 64, 6):
+        lo = int(lo)
+        sub = cols.slice(lo, lo + 64)
+        o = orc.records(an, sub, seed=seed, V=V, first_event_id=lo)
+        sel = (rec["event"] >= lo) & (rec["event"] < lo + 64)
+        part = rec[sel].copy()
+        part["event"] -= lo
+        assert_records(part, o, an, what="records events %d.." % lo)
