@@ -187,9 +187,9 @@ typedef struct {
                            fit (m_top had, m_top lep, pz_nu, |MET|) --, dilepton
                            (m_bb, m_t, m_tbar, m_ttbar); zeros when n_surv = 0           */
     uint64_t* recheck_count; /* 1: units re-evaluated in FP64 (diagnostic)              */
-    hf_record* records; /* per-cut records of an analysis with record_levels != 0, in no
-                           particular order; device memory (the device-resident entry
-                           points only: hf_submit_chunk / hf_fetch_results reject it)    */
+    hf_record* records; /* per-cut records of an analysis with record_levels != 0, in
+                           (event, level) order; device memory (the device-resident entry
+                           points only: hf_fetch_results rejects it)                      */
     uint64_t record_cap; /* records entries; records beyond it are counted, not written */
     uint64_t* n_records; /* 1 (device): records produced (may exceed record_cap)         */
 } hf_results;
