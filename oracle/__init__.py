@@ -4,5 +4,5 @@ Only the test-suite, the smoke check and the benchmark's CPU-baseline leg may
 import this package.  The product path (the CUDA library and its binding)
 never touches it.
 """
-from .oracle import (build, load, run, records, unit, philox4x32_10, unit_normals,  # noqa: F401
+from .oracle import (build, load, run, records, best_of, unit, philox4x32_10, unit_normals,  # noqa: F401
                      w_pz, w_pz_both, hadtop, ttbar, real_roots, dilep_pairing, hist_bin, mass)

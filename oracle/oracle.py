@@ -218,6 +218,44 @@ def records(an, cols, *, seed=0, V=1, first_event_id=0):
                 value=np.asarray(val, np.float64).reshape(-1, 4), run=r)
 
 
+def best_of(an, cols, *, seed=0, V=1, first_event_id=0):
+    """Best-of-variations per event (Sect. 4, ttH_sci: of the solutions over
+    the pseudo-experiments only the most probable one is kept).  Among the
+    variations of event e that pass every cut, the one whose reconstruction
+    is most probable: the smallest chi2 of the analysis's fit (the hadronic
+    chi2 of Eq. 1, or the full Eq. 1 chi2 when the analysis has the full fit)
+    for the semileptonic model, the smallest m_ttbar of the chosen solution
+    for the dilepton model (the same criterion that picks the solution within
+    a variation); ties go to the lowest variation index.
+
+    Returns dict: best_v (i32[N], -1 without a surviving variation), score
+    (f64[N], +inf without one), reco (f64[N, 4], that variation's quantities,
+    zeros without one), hist (u64[nbins+2], filled once per selected event
+    with its best variation's histogram variable).  Built on unit(): slow,
+    for small inputs."""
+    N = cols.n_events
+    nc = len(an["cuts"])
+    nb, lo, hi = an["hist"]
+    best_v = np.full(N, -1, np.int32)
+    score = np.full(N, np.inf)
+    reco = np.zeros((N, 4))
+    hist = np.zeros(nb + 2, np.uint64)
+    dilep = an["model"] == "dilep"
+    for e in range(N):
+        for v in range(V):
+            u = unit(an, cols, e, v, seed=seed, first_event_id=first_event_id)
+            if u["passed"] != nc:
+                continue
+            sc = u["q"][3] if dilep else u["q"][4]
+            if sc < score[e]:
+                score[e] = sc
+                best_v[e] = v
+                reco[e] = u["q"][:4]
+        if best_v[e] >= 0:
+            hist[hist_bin(reco[e, 0], nb, lo, hi)] += 1
+    return dict(best_v=best_v, score=score, reco=reco, hist=hist)
+
+
 def unit(an, cols, e, v, *, seed=0, first_event_id=0):
     """One unit (event e, variation v): dict(passed, idx[4], q[6])."""
     lib = load()
