@@ -6,3 +6,4 @@ never touches it.
 """
 from .oracle import (build, load, run, records, best_of, unit, philox4x32_10, unit_normals,  # noqa: F401
                      w_pz, w_pz_both, hadtop, ttbar, real_roots, dilep_pairing, hist_bin, mass)
+from . import hl  # noqa: F401,E402
