@@ -324,7 +324,8 @@ def run_ours(a):
             roofline=roof,
             cpu_baseline=cpu_base,
             e2e=e2e,
-            gpu_launches=int((2 + 13 + 1 + 1) * a.steps),
+            # per step: k_count, k_stage1, 13 stage-2 launches, k_recheck, k_finish, k_sched_update
+            gpu_launches=int((2 + 13 + 2 + 1) * a.steps),
             clocks=clocks,
             profile=dict(ms_stage1=prof["ms_stage1"] / max(1, prof["runs"]),
                          ms_stage2=s2_ms, ms_recheck=prof["ms_recheck"] / max(1, prof["runs"]),
@@ -427,7 +428,9 @@ def run_batched(a):
                 plain=dict(value=n_events / (ms_p / 1e3), ms_per_step=ms_p,
                            note="one hf_run_device_plain per chunk (one thread per event)"),
                 speedup_vs_plain=ms_p / ms_b, identical_results=bool(same), clocks=clocks, units_per_tile=tuned,
-                gpu_launches=int(6 + 13 + 1 + 2))
+                # k_bzero, k_bcount, k_bstage1, k_btiles, the dilepton grid, 13 semileptonic grids,
+                # k_brecheck, k_bfinish, one scheduler update per analysis (2)
+                gpu_launches=int(4 + 1 + 13 + 2 + 2))
     print(json.dumps(line), flush=True)
     eng.close()
 
