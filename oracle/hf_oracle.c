@@ -74,6 +74,7 @@ typedef struct {
     double sigma_jet, sigma_met;
     int32_t hist_nbins;
     double hist_lo, hist_hi;
+    double sigma_lep; /* relative lepton-energy resolution (0: leptons unsmeared) */
 } orc_analysis;
 
 /* One event, upcast to double. */
@@ -582,6 +583,7 @@ int orc_dilep_pairing(const double* l1, const double* b1, const double* l2,
 /* ------------------------------------------------------------------ */
 typedef struct {
     double jet[ORC_MAX_JETS][4]; /* smeared jets */
+    double lep[2][4];            /* smeared leptons */
     double metx, mety;           /* smeared MET */
     /* semileptonic */
     int w_done, w_ok, dneg;
@@ -601,13 +603,19 @@ static void unit_init(const orc_analysis* an, const orc_event* ev, uint64_t seed
                       uint64_t event_id, uint32_t v, orc_unit_state* st)
 {
     memset(st, 0, sizeof *st);
-    if (an->sigma_jet != 0.0 || an->sigma_met != 0.0) {
+    if (an->sigma_jet != 0.0 || an->sigma_met != 0.0 || an->sigma_lep != 0.0) {
         double z[16];
         orc_unit_normals(seed, event_id, v, z);
         for (int i = 0; i < ev->n; ++i) {
             double s = 1.0 + an->sigma_jet * z[i];
             for (int c = 0; c < 4; ++c)
                 st->jet[i][c] = s * ev->jet[i][c];
+        }
+        /* lepton l scaled by 1 + sigma_lep z[14 + l] (exactly 1 when sigma_lep = 0) */
+        for (int l = 0; l < 2; ++l) {
+            double s = 1.0 + an->sigma_lep * z[14 + l];
+            for (int c = 0; c < 4; ++c)
+                st->lep[l][c] = s * ev->lep[l][c];
         }
         st->metx = ev->met[0] + an->sigma_met * z[12];
         st->mety = ev->met[1] + an->sigma_met * z[13];
@@ -617,6 +625,9 @@ static void unit_init(const orc_analysis* an, const orc_event* ev, uint64_t seed
         for (int i = 0; i < ev->n; ++i)
             for (int c = 0; c < 4; ++c)
                 st->jet[i][c] = ev->jet[i][c];
+        for (int l = 0; l < 2; ++l)
+            for (int c = 0; c < 4; ++c)
+                st->lep[l][c] = ev->lep[l][c];
         st->metx = ev->met[0];
         st->mety = ev->met[1];
     }
@@ -627,7 +638,7 @@ static void need_w(const orc_analysis* an, const orc_event* ev, orc_unit_state* 
     if (st->w_done)
         return;
     st->w_done = 1;
-    st->w_ok = orc_w_pz(ev->lep[0], st->metx, st->mety, an->mW, &st->pz, &st->dneg);
+    st->w_ok = orc_w_pz(st->lep[0], st->metx, st->mety, an->mW, &st->pz, &st->dneg);
 }
 
 static void need_top(const orc_analysis* an, const orc_event* ev, orc_unit_state* st)
@@ -645,7 +656,7 @@ static void need_full(const orc_analysis* an, const orc_event* ev, orc_unit_stat
     if (st->f_done)
         return;
     st->f_done = 1;
-    st->fchi2 = orc_ttbar(ev->n, (const double(*)[4])st->jet, ev->lep[0], st->metx, st->mety, an->mW,
+    st->fchi2 = orc_ttbar(ev->n, (const double(*)[4])st->jet, st->lep[0], st->metx, st->mety, an->mW,
                           an->mt, an->sigma_W, an->sigma_t, st->fidx, &st->fmtop_had, &st->fmtop_lep,
                           &st->fpz);
 }
@@ -669,13 +680,13 @@ static void need_dilep(const orc_analysis* an, const orc_event* ev, orc_unit_sta
             if (b2 == b1 || !(bm >> b2 & 1u))
                 continue;
             orc_nusol sol[4];
-            int ns = orc_dilep_pairing(ev->lep[0], st->jet[b1], ev->lep[1], st->jet[b2],
+            int ns = orc_dilep_pairing(st->lep[0], st->jet[b1], st->lep[1], st->jet[b2],
                                        st->metx, st->mety, an->mW, an->mt, sol, NULL);
             for (int s = 0; s < ns; ++s) {
                 double t1[4], t2[4], w1[4], w2[4], tt[4];
-                v4_add(st->jet[b1], ev->lep[0], w1);
+                v4_add(st->jet[b1], st->lep[0], w1);
                 v4_add(w1, sol[s].nu1, t1);
-                v4_add(st->jet[b2], ev->lep[1], w2);
+                v4_add(st->jet[b2], st->lep[1], w2);
                 v4_add(w2, sol[s].nu2, t2);
                 v4_add(t1, t2, tt);
                 double mtt = orc_mass(tt);
@@ -746,7 +757,7 @@ static int cut_pass(const orc_analysis* an, int c, const orc_event* ev, orc_unit
     case ORC_NBTAG_MIN:
         return popcount12(ev->btag & ((1u << ev->n) - 1u)) >= (int)p0;
     case ORC_LEP_PT_MIN:
-        return orc_pt(ev->lep[0]) > p0;
+        return orc_pt(st->lep[0]) > p0;
     case ORC_MET_MIN:
         return sqrt(st->metx * st->metx + st->mety * st->mety) > p0;
     case ORC_WNU_SOLVABLE:
@@ -799,6 +810,7 @@ static void load_event(const orc_analysis* an, uint64_t e, const uint32_t* jet_o
 {
     int L = an->model == ORC_DILEP ? 2 : 1;
     uint32_t j0 = jet_off[e];
+    memset(ev->lep, 0, sizeof ev->lep); /* the second lepton slot stays 0 for one-lepton events */
     ev->n = (int)(jet_off[e + 1] - j0);
     for (int i = 0; i < ev->n; ++i)
         for (int c = 0; c < 4; ++c)

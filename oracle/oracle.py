@@ -34,7 +34,7 @@ class _Analysis(C.Structure):
                 ("sigma_W", C.c_double), ("mH", C.c_double),
                 ("sigma_jet", C.c_double), ("sigma_met", C.c_double),
                 ("hist_nbins", C.c_int32), ("hist_lo", C.c_double),
-                ("hist_hi", C.c_double)]
+                ("hist_hi", C.c_double), ("sigma_lep", C.c_double)]
 
 
 class _UnitResult(C.Structure):
@@ -118,6 +118,7 @@ def _analysis(an) -> _Analysis:
     a.hist_nbins = int(nb)
     a.hist_lo = _f32(lo)
     a.hist_hi = _f32(hi)
+    a.sigma_lep = _f32(an.get("sigma_lep", 0.0))
     return a
 
 

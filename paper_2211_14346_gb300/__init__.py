@@ -183,6 +183,8 @@ class DeviceResults:
 def analysis_desc(an):
     """hf_analysis_desc of a user-level analysis dict (see synth.analyses);
     returns (desc, cuts): keep cuts alive while desc is in use."""
+    if float(an.get("sigma_lep", 0.0)) != 0.0:
+        raise ValueError("lepton smearing (sigma_lep) is not implemented by the CUDA path")
     cuts = _cut_struct(an["cuts"])
     d = _lib.hf_analysis_desc()
     d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
