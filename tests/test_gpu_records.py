@@ -138,3 +138,16 @@ def test_noalloc_records(eng, orc):
     torch.cuda.synchronize()
     g = out.numpy()
     assert_records(g["records"], orc.records(an, cols, seed=13, V=4), an, what="noalloc")
+
+
+def test_many_levels_fill_several_staging_rounds(eng, orc):
+    """Sixteen cut levels, ten of them passed by every event: up to 4096
+    records per block of 256 events, written in three shared-memory rounds."""
+    cols = synth.gen_semilep(1200, 60)
+    base = analyses.config2()
+    an = analyses.with_cuts(base, [("njets_min", 0)] * 10 + list(base["cuts"]))
+    an = _rec(an, list(range(16)), ["njets", "reco0", "met", "nbtag"])
+    _, g = _run(eng, an, cols, 4, 504)
+    o = orc.records(an, cols, seed=504, V=4)
+    assert g["n_records"] == len(o["event"]) > 1200 * 10
+    assert_records(g["records"], o, an, what="16 levels")
