@@ -30,9 +30,6 @@ N_EVENTS = 10_000_000
 V = 16
 DATA_SEED = 2
 SMEAR_SEED = 1002
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
 WORKLOAD = "semilep_smeared_10M_x16"
 # DRAM bytes (read + write) of the 13 stage-2 launches of one 10M x 16 step: one ncu capture of
 # the 2M-event step (991.8 MB, dram__bytes_read.sum + dram__bytes_write.sum) scaled by the events
@@ -67,10 +64,23 @@ def _args():
 
 
 def flops_per_unit(n):
-    """Algorithmic FP32 flops of the triplet chi2 for one unit with n jets
-    (Gram formulation, FMA = 2): per jet a_i = s_i^2 G_ii (2); per pair
-    2 s_i s_j G_ij, m^2, m via rsqrt, (m - mW)/sigma, square (10); per
-    triplet candidate m^2 (3), m (2), (m - mt)/sigma (2), chi2 (2)."""
+    """Algorithmic FP32 flops of the triplet chi2 for one unit with n jets,
+    the count of the hot-path scope table: 15 per triplet candidate (the
+    smeared m^2 from the Gram terms, its root, the top term of Eq. 1 and the
+    sum) and 5 per W jet pair (its mass and W term), over the n C(n-1, 2)
+    candidates and C(n, 2) pairs of the full enumeration."""
+    if n < 3:
+        return 0
+    pairs = n * (n - 1) // 2
+    cands = n * (n - 1) * (n - 2) // 2
+    return 15 * cands + 5 * pairs
+
+
+def flops_per_unit_gram(n):
+    """The same work counted operation by operation in the Gram form (an FMA
+    = 2 flops): per jet a_i = s_i^2 G_ii (2); per pair 2 s_i s_j G_ij, m^2,
+    m via rsqrt, (m - mW)/sigma, square (10); per candidate m^2 (3), m (2),
+    (m - mt)/sigma (2), chi2 (2)."""
     if n < 3:
         return 0
     pairs = n * (n - 1) // 2
@@ -135,9 +145,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def _oracle_worker(args):
-    n_events, seed_data, lo, hi_budget, seconds = args
+def _oracle_init():
     sys.path.insert(0, ROOT)
+
+
+def _oracle_worker(args):
+    """One host process: the FP64 oracle over its own contiguous slice of
+    events for about `seconds` of CPU time, chunks of 2000 events."""
+    n_events, seed_data, lo, seconds = args
     import synth
     from synth import analyses
     import oracle
@@ -153,45 +168,72 @@ def _oracle_worker(args):
     return done, time.perf_counter() - t0
 
 
+def _oracle_step(pool, cores, seconds, step_index):
+    """One step of the oracle on the host cores: every process on a fresh
+    slice of the workload for about `seconds`.  Returns (events, s): the
+    events of all processes and the longest process's oracle time (they run
+    concurrently; generating the events is not timed)."""
+    per = max(20000, int(80000 * seconds))
+    res = pool.map(_oracle_worker, [(per, 1000 + 97 * step_index + i, (step_index * cores + i) * per, seconds)
+                                    for i in range(cores)])
+    return sum(r[0] for r in res), max(r[1] for r in res)
+
+
+def _oracle_sample(events, seconds, cores):
+    return ("%d events x %d variations of the smeared semileptonic chain per step, %d spawned processes x ~%.1f s "
+            "on contiguous slices, FP64 single-threaded oracle per process" % (events, V, cores, seconds))
+
+
 def cpu_oracle_throughput(seconds, cores=None):
     """Events/s of the FP64 oracle on the host cores: one process per core on
     its own contiguous slice of events (the multi-process pattern), each for
     about `seconds`.  Processes are spawned (no fork after CUDA init)."""
     cores = cores or os.cpu_count() or 1
-    per = max(20000, int(40000 * seconds))
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_worker, [(per, 1000 + i, i * per, per, seconds) for i in range(cores)])
-        wall = time.perf_counter() - t0
-    events = sum(r[0] for r in res)
-    busy = max(r[1] for r in res)
-    return dict(value=events / busy, unit="events/s", cores=cores, kind="oracle",
-                sample="%d events x %d variations (smeared semileptonic chain), %d spawned processes x ~%.0f s "
-                       "on contiguous slices, FP64 single-threaded oracle per process" % (events, V, cores, seconds),
-                wall_s=wall)
+    with ctx.Pool(cores, initializer=_oracle_init) as pool:
+        events, wall = _oracle_step(pool, cores, seconds, 0)
+    return dict(value=events / wall, unit="events/s", cores=cores, kind="oracle",
+                sample=_oracle_sample(events, seconds, cores), wall_s=wall)
+
+
+def headline_config(n_events):
+    """The workload description shared by both arms of the headline line."""
+    from synth import analyses
+    an = analyses.config2()
+    return dict(workload=WORKLOAD, events_per_gpu=n_events, variations=V, model="semileptonic ttbar-like",
+                smearing="jet energy x N(1, 0.10), MET + N(0, 10 GeV)", cuts=[c[0] for c in an["cuts"]],
+                l2="inputs (%.2f GB per GPU) larger than L2 (129 MB); no flush" % (127.1e-9 * n_events))
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(a):
+    """The oracle on the host cores, timed per step on a bounded sample of the
+    headline workload (the same metric, unit and configuration); each step's
+    time is the oracle time of its sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    per_step = max(2.0, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
-    vals = []
-    for i in range(a.warmup + a.steps):
-        r = cpu_oracle_throughput(per_step, cores)
-        if i >= a.warmup:
-            vals.append(r["value"])
-    v = sum(vals) / len(vals)
+    per_step = max(1.0, min(10.0, 90.0 / max(1, a.steps + a.warmup)))
+    ctx = mp.get_context("spawn")
+    events = 0
+    wall = 0.0
+    with ctx.Pool(cores, initializer=_oracle_init) as pool:
+        for i in range(a.warmup + a.steps):
+            ev, w = _oracle_step(pool, cores, per_step, i)
+            if i >= a.warmup:
+                events += ev
+                wall += w
+    v = events / wall
     line = dict(metric="events/sec", value=v, unit="events/s", n_gpus=a.gpus, steps=a.steps, warmup=a.warmup,
-                ms_per_step=1000.0 * N_EVENTS / v, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, events=N_EVENTS, variations=V, smearing="jet N(1,0.10), MET N(0,10)",
-                            note="each step times the oracle on a bounded sample of the workload"),
-                cpu_baseline=dict(value=v, unit="events/s", cores=cores, kind="oracle", sample=r["sample"]),
-                e2e=dict(value=v, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                ms_per_step=1000.0 * wall / a.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference", config=headline_config(N_EVENTS),
+                cpu_baseline=dict(value=v, unit="events/s", cores=cores, kind="oracle",
+                                  sample=_oracle_sample(events // max(1, a.steps), per_step, cores)),
+                e2e=dict(value=v, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                note="each step runs the oracle on a bounded sample of the workload (events processed per step "
+                     "in cpu_baseline.sample); ms_per_step is the oracle time of that sample (the longest of the "
+                     "concurrent processes)")
     print(json.dumps(line), flush=True)
 
 
@@ -214,7 +256,7 @@ def run_ours(a):
     from synth import analyses
     from paper_2211_14346_gb300 import build as hbuild
     hbuild.build()
-    from paper_2211_14346_gb300 import Engine, DeviceColumns, PinnedColumns, HF_FLAG_PROFILE
+    from paper_2211_14346_gb300 import Engine, DeviceColumns, PinnedColumns, HF_FLAG_PROFILE, fp32_peak
 
     N = a.events
     cols = synth.gen_semilep(N, DATA_SEED + 7919 * rank)  # each rank its own shard
@@ -226,6 +268,7 @@ def run_ours(a):
     out = eng.results_for(aid, N)
     stream = torch.cuda.current_stream()
     tuned = eng.autotune(aid, dc.slice(0, min(N, 1000000)), V=V, seed=SMEAR_SEED)  # tile shape, untimed
+    fp32 = fp32_peak(local)  # the FP32 roofline denominator, measured on this GPU (untimed)
 
     def barrier():
         if dist is not None:
@@ -264,16 +307,48 @@ def run_ours(a):
 
     # roofline of the dominant kernel (stage 2: one launch per jet multiplicity)
     s2_ms = prof["ms_stage2"] / max(1, prof["runs"])
-    flops = sum(cnt * flops_per_unit(n) for n, cnt in enumerate(prof["units_top"])) / max(1, prof["runs"])
+    runs = max(1, prof["runs"])
+    flops = sum(cnt * flops_per_unit(n) for n, cnt in enumerate(prof["units_top"])) / runs
+    flops_gram = sum(cnt * flops_per_unit_gram(n) for n, cnt in enumerate(prof["units_top"])) / runs
+    cands_enum = sum(cnt * (n * (n - 1) * (n - 2) // 2) for n, cnt in enumerate(prof["units_top"])) / runs
     achieved = flops / (s2_ms / 1000.0) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = max(fp32["tflops_ffma"], fp32["tflops_ffma2"])
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                 traffic=STAGE2_DRAM_BYTES_PER_STEP * N / N_EVENTS if V == 16 else None,
                 traffic_note="dram__bytes_read.sum + dram__bytes_write.sum of the 13 stage-2 launches of one step, "
                              "one ncu capture at 2M events scaled to this step's events",
                 kernel="k_stage2_semi<N> (13 launches per step)", ms_per_step=s2_ms,
-                peak_note="FP32 FFMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+                flops_per_step=flops,
+                flop_model="15 per triplet candidate + 5 per W jet pair over the full enumeration "
+                           "(n C(n-1,2) candidates, C(n,2) pairs) of every unit that evaluates the triplet chi2",
+                achieved_gram_model=flops_gram / (s2_ms / 1000.0) / 1e12,
+                candidates_enumerated_per_step=cands_enum,
+                candidates_evaluated_per_step=prof["cands_top"] / runs,
+                peak_note="measured by hf_fp32_peak on this GPU before the timed region: best of scalar FFMA "
+                          "(%.1f TFLOP/s) and packed FFMA2 (%.1f TFLOP/s), %d SMs; fraction of measured" % (
+                              fp32["tflops_ffma"], fp32["tflops_ffma2"], fp32["sm_count"]),
                 share_of_step=s2_ms / ms_step if ms_step else None)
+
+    # the plain one-thread-per-event form on the same chunk (the comparison of the metric)
+    out_plain = eng.results_for(aid, N)
+    eng.run_device(aid, dc, V=V, seed=SMEAR_SEED, first_event_id=first_id, out=out_plain, plain=True)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    plain_steps = 2
+    p0.record(stream)
+    for _ in range(plain_steps):
+        eng.run_device(aid, dc, V=V, seed=SMEAR_SEED, first_event_id=first_id, out=out_plain, plain=True)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = p0.elapsed_time(p1) / plain_steps
+    rp = out_plain.numpy()
+    plain = dict(value=N / (ms_plain / 1e3), unit="events/s", ms_per_step=ms_plain, steps=plain_steps,
+                 identical_results=bool(np.array_equal(rp["cutflow"], res["cutflow"]) and
+                                        np.array_equal(rp["hist"], res["hist"]) and
+                                        np.array_equal(rp["mask"], res["mask"])),
+                 note="hf_run_device_plain: one thread per event, cuts in user order, no compaction or staging, "
+                      "same FP32 bands and FP64 recheck; one warm-up run")
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -314,14 +389,12 @@ def run_ours(a):
         line = dict(
             metric="events/sec", value=value, unit="events/s", n_gpus=world, steps=a.steps, warmup=a.warmup,
             ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
-            data="synthetic",
-            config=dict(workload=WORKLOAD, events_per_gpu=N, variations=V, model="semileptonic ttbar-like",
-                        smearing="jet energy x N(1, 0.10), MET + N(0, 10 GeV)", cuts=[c[0] for c in an["cuts"]],
-                        l2="inputs (%.2f GB per GPU) larger than L2 (129 MB); no flush" % (dc.nbytes() / 1e9),
-                        fp64_recheck_units_per_step=int(res["recheck_count"]),
-                        units_per_step=N * V, cutflow=[int(x) for x in res["cutflow"]],
-                        units_per_tile=tuned),
+            data="synthetic", config=headline_config(N),
+            results=dict(fp64_recheck_units_per_step=int(res["recheck_count"]),
+                         units_per_step=N * V, cutflow=[int(x) for x in res["cutflow"]], units_per_tile=tuned),
             roofline=roof,
+            plain=plain,
+            speedup_vs_plain=ms_plain / ms_step,
             cpu_baseline=cpu_base,
             e2e=e2e,
             # per step: k_count, k_stage1, 13 stage-2 launches, k_recheck, k_finish, k_sched_update

@@ -340,6 +340,26 @@ typedef struct {
 hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
 
 /* ------------------------------------------------------------------ */
+/* Measurement.                                                         */
+/* ------------------------------------------------------------------ */
+/* Measured FP32 throughput of the device, the denominator of the FP32
+ * roofline of the reconstruction kernels (the paper has no counterpart; it
+ * reports no absolute rates).  Runs a full grid of independent fused
+ * multiply-add chains for about a second in total -- scalar fmaf and the
+ * packed two-lane fma.rn.f32x2 of sm_100 and later -- timed with CUDA events
+ * on a private stream after a warm-up launch, and writes the best of three
+ * timed launches of each (2 flops per lane per fma) and the SM count into
+ * *out (host).  Allocates and frees a few KB of device memory; restores the
+ * calling thread's current device.  Errors: HF_EINVAL (NULL out, bad
+ * device), HF_ECUDA. */
+typedef struct {
+    int32_t sm_count;     /* multiprocessors of the device                     */
+    double tflops_ffma;   /* scalar FFMA, TFLOP/s                              */
+    double tflops_ffma2;  /* packed two-lane FFMA, TFLOP/s                     */
+} hf_fp32_peak_result;
+hf_status hf_fp32_peak(int32_t device, hf_fp32_peak_result* out);
+
+/* ------------------------------------------------------------------ */
 /* Allocation-free run.                                                 */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart of this entry point: it serves callers that

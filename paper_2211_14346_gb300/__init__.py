@@ -205,6 +205,15 @@ def analysis_desc(an):
     return d, cuts
 
 
+def fp32_peak(device=0):
+    """Measured FP32 throughput of the device (hf_fp32_peak): dict(sm_count,
+    tflops_ffma, tflops_ffma2)."""
+    lib = _lib.load()
+    r = _lib.hf_fp32_peak_result()
+    _lib.check(lib.hf_fp32_peak(int(device), C.byref(r)))
+    return dict(sm_count=r.sm_count, tflops_ffma=r.tflops_ffma, tflops_ffma2=r.tflops_ffma2)
+
+
 class Engine:
     """One library context on one GPU."""
 

@@ -75,6 +75,10 @@ class hf_chunk(C.Structure):
                 ("first_event_id", C.c_uint64), ("seed", C.c_uint64), ("cols", hf_columns), ("out", hf_results)]
 
 
+class hf_fp32_peak_result(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("tflops_ffma", C.c_double), ("tflops_ffma2", C.c_double)]
+
+
 class hf_profile_data(C.Structure):
     _fields_ = [("runs", C.c_uint64), ("ms_stage1", C.c_double), ("ms_stage2", C.c_double),
                 ("ms_recheck", C.c_double), ("launches_stage2", C.c_uint64), ("units_stage2", C.c_uint64),
@@ -115,6 +119,7 @@ def load():
                                    C.POINTER(hf_results), vp], i32),
         "hf_run_batch": ([vp, C.POINTER(hf_chunk), u32, vp], i32),
         "hf_autotune": ([vp, u32, C.POINTER(hf_columns), u64, u32, u64, C.POINTER(i32)], i32),
+        "hf_fp32_peak": ([i32, C.POINTER(hf_fp32_peak_result)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -128,7 +133,8 @@ def declared_symbols():
     """Names of the entry points this binding marshals (the ones hf.h declares)."""
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
-            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch", "hf_autotune"]
+            "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch", "hf_autotune",
+            "hf_fp32_peak"]
 
 
 class HFError(RuntimeError):
