@@ -9,7 +9,8 @@ and a jet-energy scale changes neither eta nor the jet counts):
 
 - isolated lepton: no jet within Delta R < 0.4 (Delta R^2 = Delta eta^2 +
   Delta phi^2, Delta phi wrapped to [-pi, pi]);
-- eta = asinh(pz / pT); regions by |eta| of the jets: I |eta| < 2.5,
+- transverse magnitudes (pT, |MET|) are sqrt(x^2 + y^2) in FP64;
+- eta = asinh(pz / pT) (+-inf for pT = 0); regions by |eta| of the jets: I |eta| < 2.5,
   II 2.5 < |eta| < 2.75, III 2.75 < |eta| < 3.5 (boundaries and |eta| >= 3.5
   in none);
 - b-jets: b-tagged jets of region I;
@@ -38,11 +39,20 @@ from .oracle import hist_bin, unit_normals
 CHANNELS = ("none", "ttbar_1l", "ttbar_2l", "t_channel", "wt_1l", "wt_2l")
 
 
+def pt_of(x, y):
+    """Transverse magnitude sqrt(x^2 + y^2) in FP64 (the formula of the rest
+    of the oracle)."""
+    x, y = float(x), float(y)
+    return math.sqrt(x * x + y * y)
+
+
 def eta_phi(p):
-    """(eta, phi) of a (px, py, pz, E) vector in FP64."""
+    """(eta, phi) of a (px, py, pz, E) vector in FP64: eta = asinh(pz / pT),
+    +-inf along the beam (pT = 0, a jet in no region)."""
     px, py, pz = float(p[0]), float(p[1]), float(p[2])
-    pt = math.hypot(px, py)
-    return math.asinh(pz / pt), math.atan2(py, px)
+    pt = pt_of(px, py)
+    eta = math.asinh(pz / pt) if pt > 0.0 else math.copysign(math.inf, pz)
+    return eta, math.atan2(py, px)
 
 
 def delta_r(a, b):
@@ -73,8 +83,9 @@ def _mass(p):
 
 
 def classify_event(jets, btag_bits, leps, lq, lflav, metx, mety, *, met_min=30.0, mll_min=40.0, mtw_min=50.0,
-                   dr_iso=0.4):
-    """Channel code of one unit and the leading isolated lepton's pT."""
+                   dr_iso=float(np.float32(0.4))):
+    """Channel code of one unit and the leading isolated lepton's pT
+    (thresholds as given; classify rounds them to FP32 first)."""
     jep = [eta_phi(j) for j in jets]
     iso = []
     for k, l in enumerate(leps):
@@ -89,8 +100,8 @@ def classify_event(jets, btag_bits, leps, lq, lflav, metx, mety, *, met_min=30.0
         if g == 1 and (btag_bits >> i) & 1:
             nb += 1
     n1, n2, n3 = n[1], n[2], n[3]
-    met = math.hypot(metx, mety)
-    lead = max((math.hypot(float(leps[k][0]), float(leps[k][1])) for k in iso), default=0.0)
+    met = pt_of(metx, mety)
+    lead = max((pt_of(leps[k][0], leps[k][1]) for k in iso), default=0.0)
     if not met > met_min:
         return 0, lead
     if len(iso) == 1:
@@ -101,7 +112,7 @@ def classify_event(jets, btag_bits, leps, lq, lflav, metx, mety, *, met_min=30.0
         if n1 == 1 and n2 + n3 == 1 and nb == 1:
             return 3, lead
         if n1 == 3 and nb == 1 and n2 == 0 and n3 == 0:
-            mt2 = 2.0 * (math.hypot(lx, ly) * met - (lx * metx + ly * mety))
+            mt2 = 2.0 * (pt_of(lx, ly) * met - (lx * metx + ly * mety))
             if math.sqrt(max(mt2, 0.0)) > mtw_min:
                 return 4, lead
         return 0, lead
@@ -123,6 +134,7 @@ def classify(cols, *, seed=0, V=1, sigma_met=0.0, first_event_id=0, hist=(50, 0.
     (u64[5, nbins + 2], per signal channel)."""
     N = cols.n_events
     nbins, lo, hi = hist
+    cuts = {k: float(np.float32(x)) for k, x in cuts.items()}  # the C ABI carries FP32 parameters
     ch = np.zeros((N, V), np.int8)
     counts = np.zeros(6, np.uint64)
     h = np.zeros((5, nbins + 2), np.uint64)
