@@ -125,11 +125,94 @@ double orc_u01(uint32_t x)
     return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
+/* ln and sin / cos of the smearing normals.  Math libraries round these
+ * functions differently in the last place, and a decision that sits at the
+ * rounding level of a normal (a near-double root of the dilepton quartic)
+ * would then depend on the library.  The definition therefore fixes how they
+ * are evaluated: a fixed sequence of IEEE double operations (+, -, *, /, with
+ * no fused multiply-add), within about an ulp of the exact functions.
+ *
+ * ln x: x = f 2^e with f in [sqrt(1/2), sqrt(2)) (frexp, exact), ln f =
+ * 2 atanh(s) = 2 (s + s^3/3 + ... + s^23/23) with s = (f - 1) / (f + 1),
+ * |s| <= 0.1716 (the next term is below 2^-56 relative), and e ln 2 with ln 2
+ * split into a head of 32 significant bits (e times it is exact) and the
+ * rest. */
+static const double ORC_LN2_HI = 0.6931471806019545;      /* ln 2 rounded to 32 bits */
+static const double ORC_LN2_LO = -4.2009150726810846e-11; /* ln 2 - ORC_LN2_HI       */
+
+double orc_bm_log(double x)
+{
+    int e;
+    double f = frexp(x, &e); /* x = f 2^e, f in [1/2, 1) */
+    if (f < 0.70710678118654752) {
+        f = f * 2.0;
+        e = e - 1;
+    }
+    const double s = (f - 1.0) / (f + 1.0);
+    const double s2 = s * s;
+    double p = 1.0 / 23.0;
+    p = 1.0 / 21.0 + s2 * p;
+    p = 1.0 / 19.0 + s2 * p;
+    p = 1.0 / 17.0 + s2 * p;
+    p = 1.0 / 15.0 + s2 * p;
+    p = 1.0 / 13.0 + s2 * p;
+    p = 1.0 / 11.0 + s2 * p;
+    p = 1.0 / 9.0 + s2 * p;
+    p = 1.0 / 7.0 + s2 * p;
+    p = 1.0 / 5.0 + s2 * p;
+    p = 1.0 / 3.0 + s2 * p;
+    const double lf = 2.0 * s + (2.0 * s) * (s2 * p);
+    return (double)e * ORC_LN2_HI + ((double)e * ORC_LN2_LO + lf);
+}
+
+/* sin and cos of 2 pi u for u in [0, 1], u a multiple of 2^-24 (the uniforms
+ * here): q = nearest integer to 4u and r = u - q/4 (both exact, |r| <= 1/8),
+ * x = 2 pi r with 2 pi split into a head of 28 significant bits (r times it
+ * is exact) and the rest, |x| <= pi/4; Taylor series of sin to x^19 and of
+ * cos to x^18 (the next terms are below 1e-20); then the quadrant q. */
+static const double ORC_2PI_HI = 6.283185303211212;     /* 2 pi rounded to 28 bits */
+static const double ORC_2PI_LO = 3.968374318722162e-09; /* 2 pi - ORC_2PI_HI       */
+
+void orc_bm_sincos2pi(double u, double* sn, double* cs)
+{
+    const double q = floor(4.0 * u + 0.5);
+    const double r = u - 0.25 * q;
+    const double x = r * ORC_2PI_HI + r * ORC_2PI_LO;
+    const double x2 = x * x;
+    double ps = -1.0 / 121645100408832000.0;   /* -1/19! */
+    ps = 1.0 / 355687428096000.0 + x2 * ps;    /*  1/17! */
+    ps = -1.0 / 1307674368000.0 + x2 * ps;     /* -1/15! */
+    ps = 1.0 / 6227020800.0 + x2 * ps;         /*  1/13! */
+    ps = -1.0 / 39916800.0 + x2 * ps;          /* -1/11! */
+    ps = 1.0 / 362880.0 + x2 * ps;             /*  1/9!  */
+    ps = -1.0 / 5040.0 + x2 * ps;              /* -1/7!  */
+    ps = 1.0 / 120.0 + x2 * ps;                /*  1/5!  */
+    ps = -1.0 / 6.0 + x2 * ps;                 /* -1/3!  */
+    const double s0 = x + x * (x2 * ps);
+    double pc = -1.0 / 6402373705728000.0;     /* -1/18! */
+    pc = 1.0 / 20922789888000.0 + x2 * pc;     /*  1/16! */
+    pc = -1.0 / 87178291200.0 + x2 * pc;       /* -1/14! */
+    pc = 1.0 / 479001600.0 + x2 * pc;          /*  1/12! */
+    pc = -1.0 / 3628800.0 + x2 * pc;           /* -1/10! */
+    pc = 1.0 / 40320.0 + x2 * pc;              /*  1/8!  */
+    pc = -1.0 / 720.0 + x2 * pc;               /* -1/6!  */
+    pc = 1.0 / 24.0 + x2 * pc;                 /*  1/4!  */
+    const double c0 = (1.0 - 0.5 * x2) + (x2 * x2) * pc;
+    switch ((int)q & 3) {
+    case 0: *sn = s0; *cs = c0; break;
+    case 1: *sn = c0; *cs = -s0; break;
+    case 2: *sn = -s0; *cs = -c0; break;
+    default: *sn = -c0; *cs = s0; break;
+    }
+}
+
 /* The 16 standard normals of unit (seed, event, variation).
  * Counter of block b (0..3) = (b, v, event_lo32, event_hi32), key = (seed_lo32,
  * seed_hi32).  Words 2k and 2k+1 of the 16 form one Box-Muller pair:
- *   z[2k] = sqrt(-2 ln u0) cos(2 pi u1),  z[2k+1] = sqrt(-2 ln u0) sin(2 pi u1).
- * z[0..11] scale jets 0..11, z[12], z[13] shift MET x, y; z[14], z[15] unused. */
+ *   z[2k] = sqrt(-2 ln u0) cos(2 pi u1),  z[2k+1] = sqrt(-2 ln u0) sin(2 pi u1),
+ * ln, cos and sin evaluated as above.
+ * z[0..11] scale jets 0..11, z[12], z[13] shift MET x, y; z[14], z[15] scale leptons
+ * 0 and 1 when the analysis smears leptons. */
 void orc_unit_normals(uint64_t seed, uint64_t event, uint32_t v, double z[16])
 {
     uint32_t w[16];
@@ -141,10 +224,11 @@ void orc_unit_normals(uint64_t seed, uint64_t event, uint32_t v, double z[16])
     for (int k = 0; k < 8; ++k) {
         double u0 = orc_u01(w[2 * k]);
         double u1 = orc_u01(w[2 * k + 1]);
-        double r = sqrt(-2.0 * log(u0));
-        double th = 2.0 * M_PI * u1;
-        z[2 * k] = r * cos(th);
-        z[2 * k + 1] = r * sin(th);
+        double r = sqrt(-2.0 * orc_bm_log(u0));
+        double sn, cs;
+        orc_bm_sincos2pi(u1, &sn, &cs);
+        z[2 * k] = r * cs;
+        z[2 * k + 1] = r * sn;
     }
 }
 

@@ -100,6 +100,48 @@ def test_box_muller_layout_closed_form(orc):
         assert ang == pytest.approx(2 * np.pi * u[2 * k + 1], abs=1e-12)
 
 
+def _ulps(a, b):
+    """Distance in units in the last place of b."""
+    return np.abs(a - b) / np.spacing(np.abs(b))
+
+
+def test_box_muller_functions_within_an_ulp(orc):
+    """The fixed-operation ln and sin / cos of 2 pi u that define the normals,
+    against numpy's on every kind of uniform they see (multiples of 2^-24 in
+    (0, 1), quadrant boundaries, the extremes): within 1.5 ulp (the
+    truncation of the series is below 2^-56)."""
+    import ctypes as C
+    lib = orc.load()
+    lib.orc_bm_log.argtypes = [C.c_double]
+    lib.orc_bm_log.restype = C.c_double
+    lib.orc_bm_sincos2pi.argtypes = [C.c_double, C.c_void_p, C.c_void_p]
+    rng = np.random.default_rng(3)
+    k = np.concatenate([rng.integers(1, 1 << 24, 200000), [1, 2, 3, (1 << 24) - 1, 1 << 22, 1 << 23, 3 << 22,
+                                                           (1 << 22) + 1, (1 << 21) + 1, (1 << 23) - 1]])
+    u = k.astype(np.float64) / 2.0 ** 24
+    lg = np.array([lib.orc_bm_log(x) for x in u])
+    assert _ulps(lg, np.log(u)).max() <= 1.5
+    sn, cs = C.c_double(), C.c_double()
+    s_, c_ = [], []
+    for x in u:
+        lib.orc_bm_sincos2pi(x, C.byref(sn), C.byref(cs))
+        s_.append(sn.value)
+        c_.append(cs.value)
+    s_, c_ = np.array(s_), np.array(c_)
+    # reference in extended precision of the angle: 2 pi u exactly = 2 pi k / 2^24
+    import mpmath
+    mpmath.mp.prec = 120
+    pick = rng.choice(u.size, 4000, replace=False).tolist() + list(range(u.size - 10, u.size))
+    for i in pick:
+        th = 2 * mpmath.pi * mpmath.mpf(int(k[i])) / 2 ** 24
+        es, ec = float(mpmath.sin(th)), float(mpmath.cos(th))
+        tol_s = 1.5 * np.spacing(abs(es)) if abs(es) > 1e-300 else 1e-300
+        tol_c = 1.5 * np.spacing(abs(ec)) if abs(ec) > 1e-300 else 1e-300
+        assert abs(s_[i] - es) <= max(tol_s, 2.0 ** -60), (k[i], s_[i], es)
+        assert abs(c_[i] - ec) <= max(tol_c, 2.0 ** -60), (k[i], c_[i], ec)
+    assert np.abs(s_ * s_ + c_ * c_ - 1.0).max() <= 4.5e-16  # two roundings of the squares and the sum
+
+
 def test_normals_moments(orc):
     """1.6e5 normals: mean, variance, 4th moment within 5 sigma; bounded."""
     zs = np.concatenate([orc.unit_normals(1, e, v) for e in range(2000) for v in range(5)])
