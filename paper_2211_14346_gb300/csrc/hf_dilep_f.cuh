@@ -14,8 +14,10 @@
 //     the coefficients normalised (both exact scalings of the same
 //     polynomial); the sign of every level (R, R', R'') at its critical
 //     points is evaluated in FP64 and must exceed its rounding bound; each
-//     root is bracketed by FP32 bisection, polished by FP64 Newton steps and
-//     certified by an FP64 sign change across a tiny interval around it;
+//     critical point is bracketed by FP32 bisection and the bracket
+//     certified by FP64 signs at its ends (else bracketed again in FP64);
+//     each root is bracketed by FP32 bisection, polished by FP64 Newton steps
+//     and certified by an FP64 sign change across a tiny interval around it;
 //   * FP64 back-substitution, E_nu signs and masses at the certified roots.
 // Any decision the bounds cannot certify flags the unit for the FP64 recheck
 // (the full definition).
@@ -79,17 +81,18 @@ __device__ inline int real_roots_mixed(const double* R, float safety, double* ro
     }
     for (int l = 0; l <= L; ++l)
         for (int i = 0; i <= deg[l]; ++i) levf[l][i] = (float)lev[l][i];
-    double crit[4], crit_w[4];
+    double crit[4], crit_w[4], crit_d[4];  // critical points, their widths, a bound on |derivative| there
     int nc = 0;
     for (int l = L; l >= 0; --l) {
         const double* cl = lev[l];
         const float* cf = levf[l];
         const int dl = deg[l];
-        double r[4], rw[4];
+        double r[4], rw[4], rd[4];
         int nr = 0;
         if (dl == 1) {
             r[0] = -cl[0] / cl[1];
             rw[0] = 4.0e-16 * fabs(r[0]);
+            rd[0] = 0.0;
             nr = 1;
         } else {
             double pts[6];
@@ -106,7 +109,7 @@ __device__ inline int real_roots_mixed(const double* R, float safety, double* ro
                     dv = dv * crit[i] + fv;
                     fv = fv * crit[i] + cl[k];
                 }
-                bd = fabs(dv) * crit_w[i];
+                bd = fmax(fabs(dv), crit_d[i]) * crit_w[i];
                 if (!(fabs(v) > safety * (b + bd) + 1.0e-300)) return -1;
                 if (crit[i] > -1.0 && crit[i] < 1.0) pts[np++] = crit[i];
             }
@@ -128,9 +131,53 @@ __device__ inline int real_roots_mixed(const double* R, float safety, double* ro
                 }
                 double t = 0.5 * ((double)lo + (double)hi);
                 if (l > 0) {
-                    // a critical point of the level above: FP32 resolution suffices
-                    r[nr] = t;
-                    rw[nr] = (double)(hi - lo) + 1.2e-7 * fabs(t);
+                    // a critical point of the level above.  The FP32 signs near a
+                    // root of this level are rounding noise, so the FP32 bracket
+                    // counts only when the FP64 signs at its ends, beyond their
+                    // rounding bounds, differ as they should; otherwise the root
+                    // is bracketed again by FP64 bisection of the monotone
+                    // interval, and a bracket that cannot be certified sends the
+                    // unit to the FP64 recheck.
+                    double dlo = (double)lo, dhi = (double)hi;
+                    double bl, bh;
+                    double fl = peval_dd(cl, dl, dlo, &bl), fh = peval_dd(cl, dl, dhi, &bh);
+                    bool ok = fabs(fl) > safety * bl && fabs(fh) > safety * bh && (fl < 0.0) == neg &&
+                              (fh < 0.0) != neg;
+                    // widen the FP32 bracket until its ends certify (about one
+                    // step when needed), within the monotone interval
+                    double w = fmax((double)(hi - lo), 1.0e-300);
+                    for (int k = 0; k < 24 && !ok; ++k) {
+                        w *= 4.0;
+                        dlo = fmax(pts[i], (double)lo - w);
+                        dhi = fmin(pts[i + 1], (double)hi + w);
+                        fl = peval_dd(cl, dl, dlo, &bl);
+                        fh = peval_dd(cl, dl, dhi, &bh);
+                        ok = fabs(fl) > safety * bl && fabs(fh) > safety * bh && (fl < 0.0) == neg &&
+                             (fh < 0.0) != neg;
+                        if (dlo == pts[i] && dhi == pts[i + 1]) break;
+                    }
+                    if (!ok) {
+                        // FP64 bisection of the monotone interval, stopped while
+                        // the midpoint's sign is still certain
+                        dlo = pts[i];
+                        dhi = pts[i + 1];
+                        for (int it = 0; it < 64; ++it) {
+                            const double mid = 0.5 * (dlo + dhi);
+                            if (!(mid > dlo && mid < dhi)) break;
+                            double bm;
+                            const double fm = peval_dd(cl, dl, mid, &bm);
+                            if (!(fabs(fm) > safety * bm)) break;
+                            if ((fm < 0.0) == neg) dlo = mid;
+                            else dhi = mid;
+                        }
+                        fl = peval_dd(cl, dl, dlo, &bl);
+                        fh = peval_dd(cl, dl, dhi, &bh);
+                        ok = fabs(fl) > safety * bl && fabs(fh) > safety * bh && (fl < 0.0) == neg && (fh < 0.0) != neg;
+                        if (!ok) return -1;
+                    }
+                    r[nr] = 0.5 * (dlo + dhi);
+                    rw[nr] = (dhi - dlo) + 1.0e-15 * fabs(r[nr]);
+                    rd[nr] = fmax(fabs(fl) + bl, fabs(fh) + bh);  // |level| on the bracket (monotone)
                     ++nr;
                     continue;
                 }
@@ -156,12 +203,14 @@ __device__ inline int real_roots_mixed(const double* R, float safety, double* ro
                 if (!(fabs(fl) > safety * bl && fabs(fh) > safety * bh) || ((fl < 0.0) == (fh < 0.0))) return -1;
                 r[nr] = t;
                 rw[nr] = h;
+                rd[nr] = 0.0;
                 ++nr;
             }
         }
         for (int i = 0; i < nr; ++i) {
             crit[i] = r[i];
             crit_w[i] = rw[i];
+            crit_d[i] = rd[i];
         }
         nc = nr;
     }
@@ -336,11 +385,7 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
         zdone |= 1u << k;
         uint4 w = philox4x32_10(ctr_of((uint32_t)(k / 2), v, event_id), key_of(seed));
         uint32_t w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
-        double u0 = u01d(w0), u1 = u01d(w1);
-        double rr = sqrt(-2.0 * log(u0));
-        double th = (2.0 * 3.141592653589793) * u1;
-        z[2 * k] = rr * cos(th);
-        z[2 * k + 1] = rr * sin(th);
+        box_muller_d(w0, w1, z[2 * k], z[2 * k + 1]);
     };
     double jd[MAX_JETS][4];
     for (int i = 0; i < n; ++i) {

@@ -45,23 +45,100 @@ __device__ __forceinline__ double mass_d(const double* a)
     return m2 >= 0.0 ? sqrt(m2) : -sqrt(-m2);
 }
 
+// ln and the sine / cosine of 2 pi u for the FP64 smearing normals, as the
+// definition fixes them: one sequence of IEEE double operations (+, -, *, /;
+// every file is compiled with -fmad=false, so none is fused), so that the
+// normals are the same bits on every machine that runs it; within about an
+// ulp of the exact functions (math libraries differ from one another in the
+// last place, enough to move a unit that sits at a near-double root of the
+// dilepton quartic).
+//
+// ln x: x = f 2^e, f in [sqrt(1/2), sqrt(2)) (frexp is exact); ln f =
+// 2 atanh(s), s = (f - 1) / (f + 1), |s| <= 0.1716, by the odd series to
+// s^23 / 23 (Horner in s^2); plus e ln 2, ln 2 as a 32-bit head (e times it
+// exact) and its remainder.
+__device__ __forceinline__ double bm_log_d(double x)
+{
+    const double ln2_hi = 0.6931471806019545, ln2_lo = -4.2009150726810846e-11;
+    int e;
+    double f = frexp(x, &e);
+    if (f < 0.70710678118654752) {
+        f = f * 2.0;
+        e = e - 1;
+    }
+    const double s = (f - 1.0) / (f + 1.0);
+    const double s2 = s * s;
+    double p = 1.0 / 23.0;
+    p = 1.0 / 21.0 + s2 * p;
+    p = 1.0 / 19.0 + s2 * p;
+    p = 1.0 / 17.0 + s2 * p;
+    p = 1.0 / 15.0 + s2 * p;
+    p = 1.0 / 13.0 + s2 * p;
+    p = 1.0 / 11.0 + s2 * p;
+    p = 1.0 / 9.0 + s2 * p;
+    p = 1.0 / 7.0 + s2 * p;
+    p = 1.0 / 5.0 + s2 * p;
+    p = 1.0 / 3.0 + s2 * p;
+    const double lf = 2.0 * s + (2.0 * s) * (s2 * p);
+    return (double)e * ln2_hi + ((double)e * ln2_lo + lf);
+}
+
+// sin and cos of 2 pi u, u in [0, 1] a multiple of 2^-24: q = round(4u),
+// r = u - q/4 (exact, |r| <= 1/8), x = 2 pi r (2 pi as a 28-bit head, exact
+// against r, plus its remainder), |x| <= pi/4; Taylor series of sin to x^19
+// and of cos to x^18 in Horner form; quadrant from q.
+__device__ __forceinline__ void bm_sincos2pi_d(double u, double& sn, double& cs)
+{
+    const double two_pi_hi = 6.283185303211212, two_pi_lo = 3.968374318722162e-09;
+    const double q = floor(4.0 * u + 0.5);
+    const double r = u - 0.25 * q;
+    const double x = r * two_pi_hi + r * two_pi_lo;
+    const double x2 = x * x;
+    double ps = -1.0 / 121645100408832000.0;
+    ps = 1.0 / 355687428096000.0 + x2 * ps;
+    ps = -1.0 / 1307674368000.0 + x2 * ps;
+    ps = 1.0 / 6227020800.0 + x2 * ps;
+    ps = -1.0 / 39916800.0 + x2 * ps;
+    ps = 1.0 / 362880.0 + x2 * ps;
+    ps = -1.0 / 5040.0 + x2 * ps;
+    ps = 1.0 / 120.0 + x2 * ps;
+    ps = -1.0 / 6.0 + x2 * ps;
+    const double s0 = x + x * (x2 * ps);
+    double pc = -1.0 / 6402373705728000.0;
+    pc = 1.0 / 20922789888000.0 + x2 * pc;
+    pc = -1.0 / 87178291200.0 + x2 * pc;
+    pc = 1.0 / 479001600.0 + x2 * pc;
+    pc = -1.0 / 3628800.0 + x2 * pc;
+    pc = 1.0 / 40320.0 + x2 * pc;
+    pc = -1.0 / 720.0 + x2 * pc;
+    pc = 1.0 / 24.0 + x2 * pc;
+    const double c0 = (1.0 - 0.5 * x2) + (x2 * x2) * pc;
+    const int quad = (int)q & 3;
+    sn = quad == 0 ? s0 : quad == 1 ? c0 : quad == 2 ? -s0 : -c0;
+    cs = quad == 0 ? c0 : quad == 1 ? -s0 : quad == 2 ? -c0 : s0;
+}
+
+// One FP64 Box-Muller pair from two Philox words: z0 = r cos(2 pi u1),
+// z1 = r sin(2 pi u1), r = sqrt(-2 ln u0).
+__device__ __forceinline__ void box_muller_d(uint32_t w0, uint32_t w1, double& z0, double& z1)
+{
+    const double u0 = u01d(w0), u1 = u01d(w1);
+    const double r = sqrt(-2.0 * bm_log_d(u0));
+    double sn, cs;
+    bm_sincos2pi_d(u1, sn, cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
 // Smearing normals of one unit in FP64: Philox words (b, v, e_lo, e_hi),
 // Box-Muller pairs z[2k] = r cos(2 pi u1), z[2k+1] = r sin(2 pi u1).
 __device__ inline void unit_normals_d(uint64_t seed, uint64_t event, uint32_t v, double z[16])
 {
-    const double two_pi = 2.0 * 3.141592653589793;
     uint2 key = key_of(seed);
     for (uint32_t b = 0; b < 4; ++b) {
         uint4 w = philox4x32_10(ctr_of(b, v, event), key);
-        uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-        for (int k = 0; k < 2; ++k) {
-            double u0 = u01d(ww[2 * k]);
-            double u1 = u01d(ww[2 * k + 1]);
-            double r = sqrt(-2.0 * log(u0));
-            double th = two_pi * u1;
-            z[4 * b + 2 * k] = r * cos(th);
-            z[4 * b + 2 * k + 1] = r * sin(th);
-        }
+        box_muller_d(w.x, w.y, z[4 * b], z[4 * b + 1]);
+        box_muller_d(w.z, w.w, z[4 * b + 2], z[4 * b + 3]);
     }
 }
 
@@ -233,11 +310,7 @@ struct LazyUnitD {
         zdone |= 1u << k;
         uint4 w = philox4x32_10(ctr_of((uint32_t)(k / 2), v, event_id), key_of(seed));
         uint32_t w0 = (k & 1) ? w.z : w.x, w1 = (k & 1) ? w.w : w.y;
-        double u0 = u01d(w0), u1 = u01d(w1);
-        double r = sqrt(-2.0 * log(u0));
-        double th = (2.0 * 3.141592653589793) * u1;
-        z[2 * k] = r * cos(th);
-        z[2 * k + 1] = r * sin(th);
+        box_muller_d(w0, w1, z[2 * k], z[2 * k + 1]);
     }
     __device__ const double* j(int i)
     {
