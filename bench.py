@@ -50,14 +50,15 @@ def _args():
     p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
     p.add_argument("--rates", default="0.5,0.9,1.2", help="served: arrival rates as fractions of measured capacity")
     p.add_argument("--workload", default="semilep16",
-                   choices=["semilep16", "batched", "served", "dilep", "unsmeared", "fullfit", "tthsci", "records"],
+                   choices=["semilep16", "batched", "served", "dilep", "unsmeared", "fullfit", "tthsci", "records", "hl"],
                    help="semilep16: the headline (10M semileptonic events x 16 variations); "
                         "batched: uneven chunks of both models through one batched launch vs per-chunk plain runs; "
                         "served: open-loop requests with continuous batching; dilep: 2M ttH-like dilepton events x 64; "
                         "unsmeared: 10M semileptonic events, no smearing (the column-scan chain); "
                         "fullfit: 2M semileptonic events x 16 with the full Eq. 1 fit; "
                         "tthsci: 20k dilepton events x 1024 variations of a 1 %% resolution (the ttH_sci shape); "
-                        "records: the headline with per-cut variable recording at every level")
+                        "records: the headline with per-cut variable recording at every level; "
+                        "hl: the HL-LHC multi-region selection (Sect. 6.1) over 10M events, the column scan")
     p.add_argument("--chunks", type=int, default=512, help="batched: number of chunks")
     p.add_argument("--max-chunk", type=int, default=100000, help="batched: largest chunk (log-uniform from 1000)")
     return p.parse_args()
@@ -764,6 +765,77 @@ def run_single_workload(a):
     eng.close()
 
 
+def run_hl(a):
+    """The HL-LHC multi-region selection (Sect. 6.1) over device-resident
+    columns: N events (default 10,000,000; synth.hl mix, data seed 26),
+    V = 1 without smearing (the pure column scan) and the per-unit channel
+    output; a second line-internal measurement with V = 16 MET variations.
+    Roofline: algorithmic bytes = every column byte of the chunk (offsets,
+    b-tags, MET, 16 B per jet, 18 B per lepton) plus the channel bytes
+    written, over the kernel's CUDA-event time."""
+    import numpy as np
+    import torch
+    from synth.hl import gen_hllhc
+    from paper_2211_14346_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2211_14346_gb300 import Engine, HLDeviceColumns, hl_desc
+    N = a.events
+    cols = gen_hllhc(N, 26)
+    hc = HLDeviceColumns(cols)
+    eng = Engine(0)
+
+    def timed(V, sigma, steps, warmup):
+        d = hl_desc(sigma_met=sigma)
+        out = dict(counts=torch.zeros(6, dtype=torch.int64, device="cuda"),
+                   hist=torch.zeros((5, d.hist_nbins + 2), dtype=torch.int64, device="cuda"),
+                   channel=torch.zeros((N, V), dtype=torch.int8, device="cuda"))
+        for _ in range(warmup):
+            eng.run_hl(hc, d, V=V, seed=26, out=out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            eng.run_hl(hc, d, V=V, seed=26, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    clk = ClockSampler(0)
+    clk.start()
+    ms, out = timed(1, 0.0, a.steps, a.warmup)
+    clocks = clk.stop()
+    ms16, out16 = timed(16, 10.0, max(1, a.steps // 2), 1)
+    assert eng.device_error() == 0
+    counts = out["counts"].cpu().numpy().tolist()
+    col_bytes = hc.nbytes()
+    algo = col_bytes + N  # columns read once + one channel byte per unit written
+    peak = 6678.8
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+    achieved = algo / (ms / 1e3) / 1e9
+    line = dict(metric="events/sec", value=N / (ms / 1e3), unit="events/s", n_gpus=1, steps=a.steps,
+                warmup=a.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="hllhc_multiregion_10M", events=N, variations=1, jets=int(cols.jet_off[-1]),
+                            leptons=int(cols.lep_off[-1]), column_bytes=col_bytes,
+                            l2="inputs (%.2f GB) larger than L2 (129 MB); no flush" % (col_bytes / 1e9)),
+                counts=counts,
+                roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                              traffic=None, kernel="k_hl (one persistent launch)",
+                              bytes_per_event=algo / N,
+                              note="algorithmic bytes: every column byte once plus the per-unit channel output; "
+                                   "peak: measured copy bandwidth (MEASURED_PEAKS.json), fraction of measured"),
+                smeared_v16=dict(ms_per_step=ms16, events_per_s=N / (ms16 / 1e3), units_per_s=16 * N / (ms16 / 1e3),
+                                 counts=out16["counts"].cpu().numpy().tolist()),
+                gpu_launches=1, clocks=clocks)
+    print(json.dumps(line), flush=True)
+    eng.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -774,6 +846,8 @@ def main():
         run_served(a)
     elif a.workload in ("dilep", "unsmeared", "fullfit", "tthsci", "records"):
         run_single_workload(a)
+    elif a.workload == "hl":
+        run_hl(a)
     else:
         run_ours(a)
 

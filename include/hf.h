@@ -296,8 +296,13 @@ hf_status hf_autotune(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* dev_c
                       uint32_t n_variations, uint64_t seed, int32_t* units_per_tile);
 
 /* Waits for the context's stream and returns the device error word of the
- * last hf_run_device* or hf_run_batch call in *word (0 = none; bit 0 = malformed offsets or
- * n_jets > 12).  Errors: HF_ECUDA. */
+ * last hf_run_device* or hf_run_batch call in *word (0 = none).  Bit 0: malformed
+ * offsets or n_jets > 12 (those events get zero results).  Bit 1: the FP64-recheck list
+ * of the run was full; the units that did not fit were re-evaluated in FP64 inside the
+ * stage-2 kernels instead, so the results are still exact, only slower (diagnostic, not
+ * an error of the results).  Bit 2: a bounded wait of a kernel on its
+ * own asynchronous copies ran out (the run's results are then incomplete).
+ * Errors: HF_ECUDA. */
 hf_status hf_device_error(hf_ctx* ctx, uint32_t* word);
 
 /* Scheduler state of an analysis: current execution order of its cuts
@@ -340,6 +345,81 @@ typedef struct {
 hf_status hf_profile(hf_ctx* ctx, hf_profile_data* out, int32_t reset);
 
 /* ------------------------------------------------------------------ */
+/* HL-LHC multi-region top selection (Sect. 6.1).                       */
+/* ------------------------------------------------------------------ */
+/* Event columns of the selection (structure of arrays, one chunk of N
+ * events; J jets and L leptons in total).  DEVICE memory for hf_run_hl. */
+#define HF_HL_MAX_JETS 16u    /* jets per event (b-tag bits are 16 wide)          */
+#define HF_HL_MAX_LEPTONS 4u  /* leptons per event                                 */
+typedef struct {
+    const uint32_t* jet_off;  /* N+1 offsets into jets; jet_off[0] = 0              */
+    const float* jets;        /* 4*J floats (px, py, pz, E), GeV, 16-byte aligned     */
+    const uint16_t* btag;     /* N: bit i <=> jet i of the event is b-tagged          */
+    const uint32_t* lep_off;  /* N+1 offsets into the lepton columns; lep_off[0] = 0  */
+    const float* lep;         /* 4*L floats (px, py, pz, E), 16-byte aligned          */
+    const int8_t* lep_q;      /* L charges (+1 / -1)                                  */
+    const uint8_t* lep_flav;  /* L flavours (0 electron, 1 muon)                      */
+    const float* met;         /* 2*N floats: MET (x, y), GeV, 8-byte aligned           */
+    uint64_t n_jets_total;    /* J = jet_off[N]                                       */
+    uint64_t n_leptons_total; /* L = lep_off[N]                                       */
+} hf_hl_columns;
+
+/* Parameters of the selection (Sect. 6.1 values in brackets). */
+typedef struct {
+    float met_min;     /* every signal bin: |MET'| > met_min [30 GeV]                         */
+    float mll_min;     /* ttbar 2l: M_ll > mll_min [40 GeV]                                    */
+    float mtw_min;     /* Wt 1l: M_T^W > mtw_min [50 GeV]                                      */
+    float dr_iso;      /* a lepton is isolated when no jet lies within Delta R < dr_iso [0.4] */
+    float eta_bounds[3]; /* regions I |eta| < b0, II b0 < |eta| < b1, III b1 < |eta| < b2
+                            [2.5, 2.75, 3.5]; 0 < b0 < b1 < b2                               */
+    float sigma_met;   /* MET resolution per component of the variations, GeV, >= 0        */
+    uint32_t hist_nbins; /* per-channel histograms of the leading isolated lepton pT, 1..1024 */
+    float hist_lo, hist_hi;
+} hf_hl_desc;
+
+/* Channel codes. */
+#define HF_HL_NONE 0
+#define HF_HL_TTBAR_1L 1
+#define HF_HL_TTBAR_2L 2
+#define HF_HL_T_CHANNEL 3
+#define HF_HL_WT_1L 4
+#define HF_HL_WT_2L 5
+
+/* DEVICE result buffers, caller-owned; NULL fields are skipped. */
+typedef struct {
+    uint64_t* counts;  /* 6: units per channel code (HF_HL_*), overwritten              */
+    uint64_t* hist;    /* 5 * (hist_nbins + 2): channel c (1..5) at (c - 1) * (nbins + 2):
+                          [0] underflow, [1..nbins], [nbins + 1] overflow; overwritten      */
+    int8_t* channel;   /* N * V: channel code of unit (event e, variation v) at e * V + v  */
+} hf_hl_results;
+
+/* The HL-LHC multi-region top selection (Sect. 6.1) over DEVICE-resident
+ * columns, enqueued on `stream` (NULL = the context's stream).  Per unit
+ * (event, variation v < n_variations): the jets' pseudorapidity regions (a
+ * boundary, or |eta| >= b2, in none), b-jets = b-tagged jets of region I,
+ * isolated leptons (no jet within Delta R < dr_iso; Delta R^2 = Delta eta^2 +
+ * Delta phi^2, Delta phi wrapped to [-pi, pi]), then, with |MET'| > met_min:
+ * one isolated lepton -- ttbar 1l (>= 4 jets in I, exactly 2 b, none in II or
+ * III), t-channel (exactly 1 jet in I and exactly 1 in II or III, exactly 1
+ * b), Wt 1l (exactly 3 jets in I, exactly 1 b, none in II or III, M_T^W >
+ * mtw_min, M_T^W^2 = 2 (pT |MET'| - pT . MET')); two isolated leptons of
+ * opposite sign and different flavour -- ttbar 2l (>= 2 jets in I, exactly
+ * 2 b, none in II or III, M_ll > mll_min), Wt 2l (1 or 2 jets in I, exactly
+ * 1 b, none in II or III); otherwise none.  The variations smear MET only:
+ * MET' = MET + sigma_met (z12, z13), the unit's Philox normals keyed by
+ * (seed, first_event_id + e, v) as in the other event models.  A unit in a
+ * signal channel adds one entry at the leading isolated lepton's pT to that
+ * channel's histogram.  Every decision equals the FP64 definition's
+ * (FP32 with error bands, FP64 inside them).  n_events < 2^32, may be 0.
+ * Errors: HF_EINVAL (NULL or misaligned pointers, bad parameters),
+ * HF_ENOMEM, HF_ECUDA.  Events with malformed offsets, more than
+ * HF_HL_MAX_JETS jets or HF_HL_MAX_LEPTONS leptons set bit 0 of the device
+ * error word (hf_device_error), get channel 0 and are not counted. */
+hf_status hf_run_hl(hf_ctx* ctx, const hf_hl_desc* desc, const hf_hl_columns* dev_cols, uint64_t n_events,
+                    uint64_t first_event_id, uint64_t seed, uint32_t n_variations, const hf_hl_results* dev_out,
+                    void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Measurement.                                                         */
 /* ------------------------------------------------------------------ */
 /* Measured FP32 throughput of the device, the denominator of the FP32
@@ -371,13 +451,22 @@ hf_status hf_fp32_peak(int32_t device, hf_fp32_peak_result* out);
  * allocating call.  Its scratch memory is one static device array of
  * HF_NOALLOC_SCRATCH_BYTES in the library, which every GPU that loads the
  * library holds until the process exits.
+ *   - Without a context there is no device error word to read: events with
+ *     malformed offsets or more than 12 jets get zero results (mask 0,
+ *     n_surv 0, reco 0, and no entry in the cut flow, not even cutflow[0])
+ *     and the call still returns HF_OK.  Callers that need malformed columns reported run
+ *     hf_run_device on them.  The FP64-recheck list of the array holds 65,536
+ *     units; beyond that the units are re-evaluated in FP64 inside the stage-2
+ *     kernels (same results, slower).
  *   - desc, dev_cols, dev_out, stream: as for hf_define_cuts and
  *     hf_run_device (DEVICE column and result buffers, caller-owned; NULL
  *     result fields are skipped; stream NULL = the legacy default stream).
  *   - n_events <= HF_NOALLOC_MAX_EVENTS, else HF_EINVAL with a message.
  *   - The first call on a device looks up the array's device address on that
  *     device (current device at the call); make that first call before any
- *     stream capture.
+ *     stream capture.  After a cudaDeviceReset the next call on that device
+ *     finds the old address stale and looks it up again: it counts as a first
+ *     call.
  *   - Every call shares the one array and clears its counters at the start;
  *     calls whose work overlaps on the GPU (different streams, or several
  *     host threads without ordering) race and give wrong results: order them.

@@ -205,6 +205,50 @@ def analysis_desc(an):
     return d, cuts
 
 
+class HLDeviceColumns:
+    """Columns of the HL-LHC selection (synth.hl layout) as torch CUDA tensors."""
+
+    def __init__(self, cols, device="cuda"):
+        import torch
+        self.n_events = cols.n_events
+        self.n_jets_total = int(cols.jet_off[-1])
+        self.n_leptons_total = int(cols.lep_off[-1])
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+        self.jet_off = t(cols.jet_off.view(np.int32))
+        self.jets = t(np.asarray(cols.jets, np.float32).reshape(-1, 4))
+        self.btag = t(cols.btag.view(np.int16))
+        self.lep_off = t(cols.lep_off.view(np.int32))
+        self.lep = t(np.asarray(cols.lep, np.float32).reshape(-1, 4))
+        self.lep_q = t(cols.lep_q)
+        self.lep_flav = t(cols.lep_flav)
+        self.met = t(np.asarray(cols.met, np.float32).reshape(-1, 2))
+
+    def struct(self):
+        s = _lib.hf_hl_columns()
+        (s.jet_off, s.jets, s.btag, s.lep_off, s.lep, s.lep_q, s.lep_flav, s.met) = [
+            x.data_ptr() for x in (self.jet_off, self.jets, self.btag, self.lep_off, self.lep, self.lep_q,
+                                   self.lep_flav, self.met)]
+        s.n_jets_total = self.n_jets_total
+        s.n_leptons_total = self.n_leptons_total
+        return s
+
+    def nbytes(self):
+        return sum(x.numel() * x.element_size() for x in (self.jet_off, self.jets, self.btag, self.lep_off, self.lep,
+                                                           self.lep_q, self.lep_flav, self.met))
+
+
+def hl_desc(met_min=30.0, mll_min=40.0, mtw_min=50.0, dr_iso=0.4, eta_bounds=(2.5, 2.75, 3.5), sigma_met=0.0,
+            hist=(50, 0.0, 500.0)):
+    """hf_hl_desc of the HL-LHC selection (Sect. 6.1 defaults)."""
+    d = _lib.hf_hl_desc()
+    d.met_min, d.mll_min, d.mtw_min, d.dr_iso = (_f32(x) for x in (met_min, mll_min, mtw_min, dr_iso))
+    for i, b in enumerate(eta_bounds):
+        d.eta_bounds[i] = _f32(b)
+    d.sigma_met = _f32(sigma_met)
+    d.hist_nbins, d.hist_lo, d.hist_hi = int(hist[0]), _f32(hist[1]), _f32(hist[2])
+    return d
+
+
 def fp32_peak(device=0):
     """Measured FP32 throughput of the device (hf_fp32_peak): dict(sm_count,
     tflops_ffma, tflops_ffma2)."""
@@ -307,6 +351,28 @@ class Engine:
         k = C.c_int32()
         self._check(self.lib.hf_autotune(self.ctx, aid, C.byref(cs), dcols.n_events, V, seed, C.byref(k)))
         return k.value
+
+    def run_hl(self, hcols, desc=None, *, V=1, seed=0, first_event_id=0, channel=True, stream=None, out=None):
+        """The HL-LHC multi-region selection on device columns (HLDeviceColumns).
+        Returns dict of torch CUDA tensors: counts (6), hist (5, nbins + 2) and,
+        with channel=True, channel (N, V) int8."""
+        import torch
+        d = desc if desc is not None else hl_desc()
+        if out is None:
+            out = dict(counts=torch.zeros(6, dtype=torch.int64, device="cuda"),
+                       hist=torch.zeros((5, d.hist_nbins + 2), dtype=torch.int64, device="cuda"))
+            if channel:
+                out["channel"] = torch.zeros((hcols.n_events, V), dtype=torch.int8, device="cuda")
+        r = _lib.hf_hl_results()
+        r.counts = out["counts"].data_ptr()
+        r.hist = out["hist"].data_ptr()
+        r.channel = out["channel"].data_ptr() if "channel" in out else None
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+        cs = hcols.struct()
+        self._check(self.lib.hf_run_hl(self.ctx, C.byref(d), C.byref(cs), hcols.n_events, first_event_id, seed, V,
+                                       C.byref(r), stream))
+        return out
 
     def device_error(self):
         w = C.c_uint32()

@@ -75,6 +75,22 @@ class hf_chunk(C.Structure):
                 ("first_event_id", C.c_uint64), ("seed", C.c_uint64), ("cols", hf_columns), ("out", hf_results)]
 
 
+class hf_hl_columns(C.Structure):
+    _fields_ = [("jet_off", C.c_void_p), ("jets", C.c_void_p), ("btag", C.c_void_p), ("lep_off", C.c_void_p),
+                ("lep", C.c_void_p), ("lep_q", C.c_void_p), ("lep_flav", C.c_void_p), ("met", C.c_void_p),
+                ("n_jets_total", C.c_uint64), ("n_leptons_total", C.c_uint64)]
+
+
+class hf_hl_desc(C.Structure):
+    _fields_ = [("met_min", C.c_float), ("mll_min", C.c_float), ("mtw_min", C.c_float), ("dr_iso", C.c_float),
+                ("eta_bounds", C.c_float * 3), ("sigma_met", C.c_float), ("hist_nbins", C.c_uint32),
+                ("hist_lo", C.c_float), ("hist_hi", C.c_float)]
+
+
+class hf_hl_results(C.Structure):
+    _fields_ = [("counts", C.c_void_p), ("hist", C.c_void_p), ("channel", C.c_void_p)]
+
+
 class hf_fp32_peak_result(C.Structure):
     _fields_ = [("sm_count", C.c_int32), ("tflops_ffma", C.c_double), ("tflops_ffma2", C.c_double)]
 
@@ -120,6 +136,8 @@ def load():
         "hf_run_batch": ([vp, C.POINTER(hf_chunk), u32, vp], i32),
         "hf_autotune": ([vp, u32, C.POINTER(hf_columns), u64, u32, u64, C.POINTER(i32)], i32),
         "hf_fp32_peak": ([i32, C.POINTER(hf_fp32_peak_result)], i32),
+        "hf_run_hl": ([vp, C.POINTER(hf_hl_desc), C.POINTER(hf_hl_columns), u64, u64, u64, u32,
+                       C.POINTER(hf_hl_results), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -134,7 +152,7 @@ def declared_symbols():
     return ["hf_open", "hf_close", "hf_last_error", "hf_define_cuts", "hf_submit_chunk", "hf_poll",
             "hf_fetch_results", "hf_run_device", "hf_run_device_plain", "hf_device_error", "hf_sched_state",
             "hf_set_exec_order", "hf_profile", "hf_run_device_noalloc", "hf_run_batch", "hf_autotune",
-            "hf_fp32_peak"]
+            "hf_fp32_peak", "hf_run_hl"]
 
 
 class HFError(RuntimeError):

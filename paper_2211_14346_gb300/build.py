@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hf_kernels.cu", "hf_s2_semi_a.cu", "hf_s2_semi_b.cu", "hf_s2_semi_c.cu", "hf_s2_semi_d.cu",
            "hf_s2_semi_e.cu", "hf_s2_semi_f.cu", "hf_s2_semi_g.cu", "hf_s2_semi_h.cu", "hf_plain.cu", "hf_plain_dilep.cu",
            "hf_stage2_dilep.cu", "hf_sched.cu", "hf_api.cpp", "hf_noalloc.cu", "hf_batch.cu",
-           "hf_probe.cu"]
+           "hf_probe.cu", "hf_hl.cu"]
 
 
 def _nvcc():

@@ -1027,12 +1027,11 @@ namespace {
 // Smallest power of two >= x (at least 4 KB): shared-memory sizes of the
 // stage-2 grids are rounded to these classes so that batches with similar
 // variation counts share one captured launch sequence.
-size_t smem_class(size_t x)
-{
-    size_t c = 4096;
-    while (c < x) c <<= 1;
-    return c;
-}
+// Shared-memory class of a batch's stage-2 kernels (part of the captured
+// graph's key): rounded up to 4 KB, so that a few classes cover all batches
+// while a class never exceeds what the largest tile needs by more than 4 KB
+// (powers of two overshot the per-block limit for the largest tiles).
+size_t smem_class(size_t x) { return (x + 4095) & ~(size_t)4095; }
 
 // Enqueues one batch on st (ctx->mu held): validation, tables, upload and the
 // captured launch sequence (captured on first use of its shape).
@@ -1532,5 +1531,88 @@ extern "C" hf_status hf_autotune(hf_ctx* ctx, uint32_t analysis_id, const hf_col
     }
     slot = best;
     if (units_per_tile) *units_per_tile = best;
+    return HF_OK;
+}
+
+// ------------------------------------------------------------------ HL-LHC selection
+extern "C" hf_status hf_run_hl(hf_ctx* ctx, const hf_hl_desc* d, const hf_hl_columns* c, uint64_t N,
+                               uint64_t first_event_id, uint64_t seed, uint32_t V, const hf_hl_results* out,
+                               void* stream)
+{
+    if (!ctx || !d || !c) return fail(HF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (hf_status s = use_device(ctx)) return s;
+    if (V < 1 || V > HF_MAX_VARIATIONS) return fail(HF_EINVAL, "n_variations must be 1..4096");
+    if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per call");
+    if (d->hist_nbins < 1 || d->hist_nbins > MAX_BINS || !(d->hist_lo < d->hist_hi))
+        return fail(HF_EINVAL, "histogram: 1..1024 bins and hist_lo < hist_hi");
+    if (!(d->eta_bounds[0] > 0.0f && d->eta_bounds[0] < d->eta_bounds[1] && d->eta_bounds[1] < d->eta_bounds[2] &&
+          d->eta_bounds[2] < 20.0f))
+        return fail(HF_EINVAL, "eta_bounds must satisfy 0 < b0 < b1 < b2 < 20");
+    if (!(d->dr_iso > 0.0f) || !(d->sigma_met >= 0.0f) || !(d->met_min >= 0.0f) || !(d->mll_min >= 0.0f) ||
+        !(d->mtw_min >= 0.0f))
+        return fail(HF_EINVAL, "thresholds must be >= 0 (dr_iso > 0)");
+    if (N > 0 && (!c->jet_off || !c->btag || !c->lep_off || !c->met || (c->n_jets_total && !c->jets) ||
+                  (c->n_leptons_total && (!c->lep || !c->lep_q || !c->lep_flav))))
+        return fail(HF_EINVAL, "a column pointer is NULL");
+    if (((uintptr_t)c->jets & 15) || ((uintptr_t)c->lep & 15) || ((uintptr_t)c->met & 7) ||
+        ((uintptr_t)c->jet_off & 3) || ((uintptr_t)c->lep_off & 3) || ((uintptr_t)c->btag & 1))
+        return fail(HF_EINVAL, "jets/lep must be 16-byte, met 8-byte, offsets 4-byte and btag 2-byte aligned");
+    if (out && (((uintptr_t)out->counts & 7) || ((uintptr_t)out->hist & 7)))
+        return fail(HF_EINVAL, "counts and hist must be 8-byte aligned");
+    HLPlan H;
+    memset(&H, 0, sizeof H);
+    H.met_min = d->met_min;
+    H.mll_min = d->mll_min;
+    H.mtw_min = d->mtw_min;
+    H.dr2 = (float)((double)d->dr_iso * (double)d->dr_iso);
+    H.dmet_min = d->met_min;
+    H.dmll_min = d->mll_min;
+    H.dmtw_min = d->mtw_min;
+    H.ddr_iso = d->dr_iso;
+    for (int b = 0; b < 3; ++b) {
+        H.deta[b] = d->eta_bounds[b];
+        H.sh[b] = (float)std::sinh((double)d->eta_bounds[b]);
+    }
+    H.smear = d->sigma_met != 0.0f;
+    H.sigma_met = d->sigma_met;
+    H.dsigma_met = d->sigma_met;
+    H.z_rel = 4.0e-7f;
+    H.safety = 4.0f;
+    H.nbins = (int)d->hist_nbins;
+    H.lo = d->hist_lo;
+    H.hi = d->hist_hi;
+    H.w = (float)(((double)d->hist_hi - (double)d->hist_lo) / d->hist_nbins);
+    H.dlo = d->hist_lo;
+    H.dhi = d->hist_hi;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_comp;
+    // the small counter block at the arena's start holds the error word; the
+    // counts and histograms the caller skips go after it
+    const size_t off_counts = 256, off_hist = off_counts + 64, bytes = off_hist + 8 * 5 * (MAX_BINS + 2);
+    if (hf_status s = ensure_arena(ctx, bytes)) return s;
+    if (ctx->arena_free) HF_CUDA(cudaStreamWaitEvent(st, ctx->arena_free, 0));
+    HLOut O;
+    O.counts = (out && out->counts) ? (unsigned long long*)out->counts : (unsigned long long*)(ctx->arena + off_counts);
+    O.hist = (out && out->hist) ? (unsigned long long*)out->hist : (unsigned long long*)(ctx->arena + off_hist);
+    O.channel = out ? out->channel : nullptr;
+    O.err = (unsigned*)(ctx->arena + SM_ERR);
+    HF_CUDA(cudaMemsetAsync(ctx->arena, 0, 256, st));
+    HF_CUDA(cudaMemsetAsync(O.counts, 0, 8 * 6, st));
+    HF_CUDA(cudaMemsetAsync(O.hist, 0, 8 * 5 * (size_t)(d->hist_nbins + 2), st));
+    HLCols C;
+    C.jet_off = c->jet_off;
+    C.jets = (const float4*)c->jets;
+    C.btag = c->btag;
+    C.lep_off = c->lep_off;
+    C.lep = (const float4*)c->lep;
+    C.lep_q = c->lep_q;
+    C.lep_flav = c->lep_flav;
+    C.met = (const float2*)c->met;
+    C.n_jets = c->n_jets_total;
+    C.n_leps = c->n_leptons_total;
+    HF_CUDA(launch_hl(H, C, (uint32_t)N, V, seed, first_event_id, O, ctx->sms, st));
+    if (!ctx->arena_free) HF_CUDA(cudaEventCreateWithFlags(&ctx->arena_free, cudaEventDisableTiming));
+    HF_CUDA(cudaEventRecord(ctx->arena_free, st));
+    if (ctx->flags & HF_FLAG_DEBUG_SYNC) HF_CUDA(cudaStreamSynchronize(st));
     return HF_OK;
 }

@@ -675,92 +675,112 @@ static __device__ __noinline__ void store_maxf(const int* uf, uint32_t V, uint8_
     }
 }
 
-// Per-event reduction of a tile's units: compensated sums of the surviving
-// units' reconstructed quantities; events without flagged units are written,
-// the others get a pending slot and their flagged units go to the recheck
-// list.  Fewer than 32 variations: one thread per event, in variation order;
-// otherwise one warp per event (lanes strided over the variations, a fixed
-// combining tree), so that a single event of up to 4096 variations does not
-// serialise the tile.  rank and size describe the calling group (size a
-// multiple of 32, every thread calls).
-__device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
-                                          uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
-                                          const uint32_t* bits, const int* uf, const float4* ureco,
-                                          unsigned long long* fc, unsigned* hist, int rank, int size)
+// Compensated sum and count over the G lanes of a lane group (G a power of
+// two <= 32; fixed tree, the group's first lane holds the totals).  Every
+// lane of the warp calls it.
+template <int G>
+__device__ __forceinline__ void group_merge4(float4& s, float4& c, unsigned& n)
 {
-    if (V < 32) {
-        for (int ev = rank; ev < ne; ev += size) {
-            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
-            unsigned cnt = 0;
-            int nflag = 0;
-            uint16_t vs[32];
-            const uint32_t e = evid[ev];
-            for (uint32_t v = 0; v < V; ++v) {
-                const int u = ev * (int)V + (int)v;
-                const int f = uf[u];
-                if (f < 0) {
-                    vs[nflag++] = (uint16_t)v;
-                } else if (f == P.n_cuts) {
-                    ++cnt;
-                    acc4(sum, comp, ureco[u]);
-                }
-            }
-            if (O.maxf) store_maxf(uf + ev * (int)V, V, O.maxf + e, false);
-            if (nflag == 0) write_event(O, e, cnt, sum, comp);
-            else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
-        }
-        return;
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) {
+        float4 s2, c2;
+        s2.x = __shfl_down_sync(0xffffffffu, s.x, o, G);
+        s2.y = __shfl_down_sync(0xffffffffu, s.y, o, G);
+        s2.z = __shfl_down_sync(0xffffffffu, s.z, o, G);
+        s2.w = __shfl_down_sync(0xffffffffu, s.w, o, G);
+        c2.x = __shfl_down_sync(0xffffffffu, c.x, o, G);
+        c2.y = __shfl_down_sync(0xffffffffu, c.y, o, G);
+        c2.z = __shfl_down_sync(0xffffffffu, c.z, o, G);
+        c2.w = __shfl_down_sync(0xffffffffu, c.w, o, G);
+        const unsigned n2 = __shfl_down_sync(0xffffffffu, n, o, G);
+        merge4(s, c, s2, c2);
+        n += n2;
     }
+}
+
+template <int G>
+__device__ __forceinline__ int group_max(int x)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o, G));
+    return x;
+}
+
+// Per-event reduction by groups of G lanes (G = 8, 16 or 32): lanes strided
+// over the event's variations, a fixed combining tree per group, so that the
+// events of a tile are reduced in parallel rather than one thread per event
+// in turn.  rank and size describe the calling group of threads (size a
+// multiple of 32, every thread calls).
+template <int G>
+__device__ inline void reduce_events_grp(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+                                         uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
+                                         const uint32_t* bits, const int* uf, const float4* ureco,
+                                         unsigned long long* fc, unsigned* hist, int rank, int size)
+{
     const unsigned lane = (unsigned)rank & 31u;
-    const unsigned below = (1u << lane) - 1u;
-    for (int ev = rank >> 5; ev < ne; ev += size >> 5) {
-        const uint32_t e = evid[ev];
+    const unsigned gl = lane & (unsigned)(G - 1);
+    const unsigned g0 = lane - gl;                            // first lane of the group
+    const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    const unsigned below = (1u << gl) - 1u;
+    constexpr int GPW = 32 / G;                               // groups per warp
+    const int gid = (rank >> 5) * GPW + (int)(lane / G);
+    const int ngroups = (size >> 5) * GPW;
+    for (int ev0 = 0; ev0 < ne; ev0 += ngroups) {
+        const int ev = ev0 + gid;
+        const bool valid = ev < ne;
+        const uint32_t e = valid ? evid[ev] : 0u;
         const int u0 = ev * (int)V;
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
         unsigned cnt = 0, nflag = 0;
-        for (uint32_t v0 = 0; v0 < V; v0 += 32) {
-            const uint32_t v = v0 + lane;
-            const int f = v < V ? uf[u0 + (int)v] : -1;
-            nflag += __popc(__ballot_sync(0xffffffffu, v < V && f < 0));
-            if (v < V && f == P.n_cuts) {
+        int mf = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            const bool in = valid && v < V;
+            const int f = in ? uf[u0 + (int)v] : -1;
+            nflag += __popc((__ballot_sync(0xffffffffu, in && f < 0) >> g0) & gbits);
+            if (in && f == P.n_cuts) {
                 ++cnt;
                 acc4(sum, comp, ureco[u0 + (int)v]);
             }
+            mf = max(mf, f);
         }
-        warp_merge4(sum, comp, cnt);
-        if (O.maxf) store_maxf(uf + u0, V, O.maxf + e, true);
-        if (nflag == 0) {
-            if (lane == 0) write_event(O, e, cnt, sum, comp);
-            continue;
+        group_merge4<G>(sum, comp, cnt);
+        if (O.maxf) {
+            mf = group_max<G>(mf);
+            if (valid && gl == 0) O.maxf[e] = (uint8_t)max(mf, 0);
         }
+        // nflag and valid are the same on a group's lanes, not across the warp:
+        // every lane runs the shuffles and ballots below, the writes are guarded
+        if (nflag == 0 && valid && gl == 0) write_event(O, e, cnt, sum, comp);
+        if (!__any_sync(0xffffffffu, nflag != 0 && valid)) continue;
         unsigned base = 0, slot = 0;
         int ok = 0;
-        if (lane == 0) ok = reserve_pending(S, nflag, cnt, sum, comp, base, slot);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (ok) {
-            for (uint32_t v0 = 0; v0 < V; v0 += 32) {
-                const uint32_t v = v0 + lane;
-                const bool fl = v < V && uf[u0 + (int)v] < 0;
-                const unsigned m = __ballot_sync(0xffffffffu, fl);
-                if (fl) S.rc[base + __popc(m & below)] = rc_entry(S, e, v, bits[ev], slot);
-                base += __popc(m);
-            }
-            continue;
+        if (nflag && valid && gl == 0) ok = reserve_pending(S, nflag, cnt, sum, comp, base, slot);
+        ok = __shfl_sync(0xffffffffu, ok, g0);
+        base = __shfl_sync(0xffffffffu, base, g0);
+        slot = __shfl_sync(0xffffffffu, slot, g0);
+        const bool listed = nflag && valid && ok;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            const bool fl = listed && v < V && uf[u0 + (int)v] < 0;
+            const unsigned m = (__ballot_sync(0xffffffffu, fl) >> g0) & gbits;
+            if (fl) S.rc[base + __popc(m & below)] = rc_entry(S, e, v, bits[ev], slot);
+            base += __popc(m);
         }
-        // list full: the lanes evaluate the flagged units in FP64
+        // list full: the group's lanes evaluate the flagged units in FP64
+        const bool inline_fp64 = nflag && valid && !ok;
+        if (!__any_sync(0xffffffffu, inline_fp64)) continue;
         float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = s2;
         unsigned n2 = 0;
-        int mf = 0;
-        for (uint32_t v0 = 0; v0 < V; v0 += 32) {
-            const uint32_t v = v0 + lane;
-            if (v < V && uf[u0 + (int)v] < 0) {
+        int mf2 = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            if (inline_fp64 && v < V && uf[u0 + (int)v] < 0) {
                 float4 reco;
                 int bin = 0;
                 const int f2 = unit_fp64(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin);
                 atomicAdd(&fc[f2], 1ull);
-                mf = max(mf, f2);
+                mf2 = max(mf2, f2);
                 if (f2 == P.n_cuts) {
                     ++n2;
                     atomicAdd(&hist[bin], 1u);
@@ -769,14 +789,60 @@ __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Ou
             }
         }
         __syncwarp();
-        warp_merge4(s2, c2, n2);
-        mf = __reduce_max_sync(0xffffffffu, mf);
-        if (lane == 0) {
-            if (O.maxf) O.maxf[e] = (uint8_t)max((int)O.maxf[e], mf);
+        group_merge4<G>(s2, c2, n2);
+        mf2 = group_max<G>(mf2);
+        if (inline_fp64 && gl == 0) {
+            if (O.maxf) O.maxf[e] = (uint8_t)max((int)O.maxf[e], mf2);
             merge4(sum, comp, s2, c2);
             atomicAdd(O.rc_total, (unsigned long long)nflag);
             write_event(O, e, cnt + n2, sum, comp);
         }
+    }
+}
+
+// Per-event reduction of a tile's units: compensated sums of the surviving
+// units' reconstructed quantities; events without flagged units are written,
+// the others get a pending slot and their flagged units go to the recheck
+// list.  Fewer than 5 variations: one thread per event, in variation order;
+// otherwise a group of 8, 16 or 32 lanes per event (reduce_events_grp), so
+// that no thread walks many variations while the others wait.  rank and size
+// describe the calling group (size a multiple of 32, every thread calls).
+__device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+                                          uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
+                                          const uint32_t* bits, const int* uf, const float4* ureco,
+                                          unsigned long long* fc, unsigned* hist, int rank, int size)
+{
+    if (V > 16) {
+        reduce_events_grp<32>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, fc, hist, rank, size);
+        return;
+    }
+    if (V > 8) {
+        reduce_events_grp<16>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, fc, hist, rank, size);
+        return;
+    }
+    if (V > 4) {
+        reduce_events_grp<8>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, fc, hist, rank, size);
+        return;
+    }
+    for (int ev = rank; ev < ne; ev += size) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f), comp = sum;
+        unsigned cnt = 0;
+        int nflag = 0;
+        uint16_t vs[4];
+        const uint32_t e = evid[ev];
+        for (uint32_t v = 0; v < V; ++v) {
+            const int u = ev * (int)V + (int)v;
+            const int f = uf[u];
+            if (f < 0) {
+                vs[nflag++] = (uint16_t)v;
+            } else if (f == P.n_cuts) {
+                ++cnt;
+                acc4(sum, comp, ureco[u]);
+            }
+        }
+        if (O.maxf) store_maxf(uf + ev * (int)V, V, O.maxf + e, false);
+        if (nflag == 0) write_event(O, e, cnt, sum, comp);
+        else pend_event(P, C, O, S, e, first_id + e, seed, bits[ev], cnt, sum, comp, vs, nflag, fc, hist);
     }
 }
 
@@ -806,6 +872,7 @@ struct TileSmem {
     uint32_t* bits; // [ev]
     float4* ureco;  // [unit]
     int* uf;        // [unit] f or -1
+    char* top;      // the chi2 step's region (16-byte aligned, after the above)
 };
 
 __host__ __device__ inline size_t tile_smem_bytes(int ev, int units, int gst)
@@ -816,6 +883,7 @@ __host__ __device__ inline size_t tile_smem_bytes(int ev, int units, int gst)
 __device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap, int gst)
 {
     TileSmem t;
+    t.top = p + ((tile_smem_bytes(ev_cap, unit_cap, gst) + 15) & ~(size_t)15);
     t.ureco = (float4*)p; p += (size_t)unit_cap * 16;
     t.lep = (float4*)p; p += (size_t)ev_cap * 16;
     t.met = (float2*)p; p += (size_t)ev_cap * 8;
@@ -824,6 +892,42 @@ __device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap, int gst)
     t.bits = (uint32_t*)p; p += (size_t)ev_cap * 4;
     t.uf = (int*)p;
     return t;
+}
+
+// Shared memory of the chi2 step of a tile (after the TileSmem region).
+constexpr int HT_UNITS = 256;  // units per sub-batch of the split evaluation
+
+struct TopSmem {
+    TopIn* tin;          // [HT_UNITS] MET state in, chi2 result out
+    uint32_t* hidx;      // [HT_UNITS] unit (index in the tile) of each listed entry
+    float* qs;           // [N * N][HT_SLOTS] smeared Gram terms, one column per thread
+    float* as;           // [N][HT_SLOTS]
+    uint8_t* pair_code;  // [npairs(MAX_JETS)]
+    unsigned* nh;        // listed units
+};
+
+__host__ __device__ constexpr size_t top_smem_bytes(int n)
+{
+    return n >= 3 ? (size_t)HT_UNITS * (sizeof(TopIn) + 4) + (size_t)(n * n + n) * HT_SLOTS * 4 + 128 : 0;
+}
+
+__device__ inline TopSmem carve_top(char* p, int n)
+{
+    TopSmem t;
+    t.tin = (TopIn*)p; p += (size_t)HT_UNITS * sizeof(TopIn);
+    t.qs = (float*)p; p += (size_t)n * n * HT_SLOTS * 4;
+    t.as = (float*)p; p += (size_t)n * HT_SLOTS * 4;
+    t.hidx = (uint32_t*)p; p += (size_t)HT_UNITS * 4;
+    t.pair_code = (uint8_t*)p; p += 96;
+    t.nh = (unsigned*)p;
+    return t;
+}
+
+// Dynamic shared memory of a semileptonic stage-2 tile (multiplicity n).
+__host__ __device__ inline size_t semi_smem_bytes(int n, bool full, int ev, int units)
+{
+    const size_t t = (tile_smem_bytes(ev, units, gram_stride(n)) + 15) & ~(size_t)15;
+    return full ? t : t + top_smem_bytes(n);
 }
 
 }  // namespace hf

@@ -37,7 +37,7 @@ enum : int { MODEL_SEMILEP = 1, MODEL_DILEP = 2 };
 enum : int { PROF_UNITS = 0, PROF_EVENTS = 1, PROF_PAIRINGS = 2, PROF_CANDS = 3, PROF_TOP = 16, PROF_DILEP = 32 };
 
 // Error word bits (device -> host).
-enum : unsigned { ERR_COLUMNS = 1u, ERR_RECHECK_FULL = 2u };
+enum : unsigned { ERR_COLUMNS = 1u, ERR_RECHECK_FULL = 2u, ERR_TIMEOUT = 4u };
 
 // Variables of the per-cut recording (values of HF_VAR_*).
 enum : int { VAR_NONE = 0, VAR_NJETS = 1, VAR_NBTAG = 2, VAR_LEP_PT = 3, VAR_MET = 4, VAR_RECO0 = 5 };
@@ -136,6 +136,42 @@ struct Scratch {
     const int* exec2;     // [MAX_CUTS] device execution order of stage-2 cuts (or null)
     int n_exec2;
     uint32_t chunk;       // chunk index recorded in recheck entries (batched runs)
+};
+
+// ------------------------------------------------------------------ HL-LHC selection
+// The HL-LHC multi-region selection (hf_hl.cu): parameters in FP32 and, for
+// the FP64 definition, in double (the same values).
+struct HLPlan {
+    float met_min, mll_min, mtw_min, dr2;   // dr2 = dr_iso^2 (FP32)
+    double dmet_min, dmll_min, dmtw_min, ddr_iso;
+    double deta[3];                         // region boundaries of |eta|
+    float sh[3];                            // sinh of the boundaries, rounded to FP32
+    int smear;
+    float sigma_met;
+    double dsigma_met;
+    float z_rel, safety;
+    int nbins;
+    float lo, hi, w;
+    double dlo, dhi;
+};
+
+struct HLCols {
+    const uint32_t* jet_off;
+    const float4* jets;
+    const uint16_t* btag;
+    const uint32_t* lep_off;
+    const float4* lep;
+    const int8_t* lep_q;
+    const uint8_t* lep_flav;
+    const float2* met;
+    uint64_t n_jets, n_leps;
+};
+
+struct HLOut {
+    unsigned long long* counts;  // [6]
+    unsigned long long* hist;    // [5][nbins + 2]
+    int8_t* channel;             // [N * V] or null
+    unsigned* err;
 };
 
 // ------------------------------------------------------------------ batched runs

@@ -17,6 +17,10 @@
 #include "hf_common.cuh"
 #include "hf_kernels.h"
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace hf {
 
 // ------------------------------------------------------------------ k_count
@@ -161,7 +165,28 @@ __global__ void __launch_bounds__(BLOCK) k_finish(const Plan P, const Cols C, co
 }
 
 // ------------------------------------------------------------------ host launchers
-size_t semi_tile_bytes(int n, int ept, int units) { return tile_smem_bytes(ept, units, gram_stride(n)); }
+// The larger of the two layouts (with and without the chi2 step), so that a
+// batch's kernels of either kind fit.
+size_t semi_tile_bytes(int n, int ept, int units) { return semi_smem_bytes(n, false, ept, units); }
+
+cudaError_t ensure_smem_attr(const void* fn)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, fn})) return cudaSuccess;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    done.insert({dev, fn});
+    return cudaSuccess;
+}
 
 int ev_per_tile_for(uint32_t V, int upt)
 {

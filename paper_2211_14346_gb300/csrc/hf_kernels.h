@@ -14,6 +14,11 @@ hf_status build_plan(const hf_analysis_desc* d, Plan& P);
 hf_status set_error(hf_status s, const char* msg);
 hf_status set_cuda_error(cudaError_t e, const char* what);
 
+// Raises the dynamic shared-memory limit of kernel fn to the device's opt-in
+// maximum, once per (current device, kernel); thread-safe.  The attribute
+// belongs to the device, so every device that launches fn needs its own call.
+cudaError_t ensure_smem_attr(const void* fn);
+
 // Events per tile of the semileptonic stage-2 kernels for V variations per
 // event and `upt` units per tile (0 = the default, UNITS_PER_TILE).
 int ev_per_tile_for(uint32_t V, int upt = 0);
@@ -71,6 +76,11 @@ size_t semi_tile_bytes(int n, int ept, int units);
 size_t dl_smem_bytes(int ev, int units);
 // Events per tile of the dilepton stage-2 kernel (upt: units per tile, 0 = default).
 int dl_ev_per_tile(uint32_t V, int upt = 0);
+
+// HL-LHC multi-region selection (hf_hl.cu): one persistent launch.  O.counts,
+// O.hist and O.err must be zeroed beforehand.
+cudaError_t launch_hl(const HLPlan& H, const HLCols& C, uint32_t N, uint32_t V, uint64_t seed, uint64_t first_id,
+                      const HLOut& O, int sms, cudaStream_t st);
 
 // Kernel launches of one fast-path run (count, stage 1, one per multiplicity, recheck).
 constexpr int FAST_LAUNCHES = 2 + NBUCKET + 1;

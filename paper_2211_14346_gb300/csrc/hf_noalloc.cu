@@ -54,11 +54,23 @@ unsigned char* g_addr[MAX_DEVICES];  // device address of the array, per device
 int g_sms[MAX_DEVICES];
 
 // Device address of the scratch array on the current device (set up once per
-// device: the name g_noalloc_scratch is only a host-side stand-in).
+// device: the name g_noalloc_scratch is only a host-side stand-in).  A cached
+// address is checked against the runtime's record of device pointers first:
+// after a reset of the device (cudaDeviceReset) the module is loaded again,
+// the old address no longer belongs to any allocation, and it is looked up
+// anew.  Neither call allocates.
 hf_status scratch_for_device(int dev, unsigned char** out, int* sms)
 {
     if (dev < 0 || dev >= MAX_DEVICES) return set_error(HF_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(g_mu);
+    if (g_addr[dev]) {
+        cudaPointerAttributes pa;
+        const cudaError_t e = cudaPointerGetAttributes(&pa, g_addr[dev]);
+        if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != dev) {
+            cudaGetLastError();
+            g_addr[dev] = nullptr;
+        }
+    }
     if (!g_addr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);

@@ -122,6 +122,121 @@ __device__ __forceinline__ void hadtop_f(const Plan& P, const float* __restrict_
     }
 }
 
+// Same result as hadtop_f (clamped minimum and second minimum, the masses of
+// the minimising candidate) with the smeared Gram terms in shared memory and
+// the W pairs pruned exactly.  A candidate's chi2 is fmaf(dt, dt, cw) >= cw for
+// the W term cw of its pair, so a pair with cw >= cap has no candidate below
+// the cap and is skipped as a whole; about a third of the pairs remain.  The
+// pair phase (unrolled over the N(N-1)/2 pairs) writes the full symmetric
+// matrix Q_ik = 2 s_i s_k G_ik with Q_ii = HT_BIG and the diagonal terms
+// A_i = s_i^2 G_ii to this thread's column of qs / as (element e at
+// e * BLOCK), and marks the pairs below the cap; the candidate loop then runs
+// over the marked pairs only (any order: the minimum and the second minimum
+// of a set do not depend on it), with the b-jet k unrolled:
+//   m^2 = ((m^2_ij + A_k) + Q_ik) + Q_jk,
+// a sum of non-negative terms (the hadtop_f error bound holds).  For k = i or
+// k = j one term is HT_BIG, so that candidate lands far above the cap and
+// never changes the result, without a branch.  Each thread reads only its own
+// column, so the loads are free of bank conflicts.  pair_code[p] = i | j << 4
+// for the pair index p = j (j - 1) / 2 + i.
+constexpr float HT_BIG = 1.0e30f;
+constexpr int HT_SLOTS = BLOCK;  // threads (and Q columns) of a chi2 round
+
+__host__ __device__ constexpr int npairs(int n) { return n * (n - 1) / 2; }
+
+template <int N>
+__device__ __forceinline__ void hadtop_pruned(const Plan& P, const float* __restrict__ gf,
+                                              const float (&s)[N > 0 ? N : 1], float cap, float* qs, float* as,
+                                              const uint8_t* pair_code, float& b1, float& b2, float& mt_b,
+                                              float& mw_b, unsigned* cands)
+{
+    b1 = cap;
+    b2 = cap;
+    mt_b = 0.0f;
+    mw_b = 0.0f;
+    if constexpr (N >= 3) {
+        constexpr int NP = npairs(N);
+        const float c_t = -P.mt * P.inv_sigma_t;
+        const float c_w = -P.mW * P.inv_sigma_W;
+        float a[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            a[i] = __fmul_rn(__fmul_rn(s[i], s[i]), gf[tri(i, i)]);
+            as[i * HT_SLOTS] = a[i];
+            qs[(i * N + i) * HT_SLOTS] = HT_BIG;
+        }
+        unsigned long long mlo = 0ull;
+        unsigned mhi = 0u;
+#pragma unroll
+        for (int j = 1; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < j; ++i) {
+                const float q = 2.0f * __fmul_rn(__fmul_rn(s[i], s[j]), gf[tri(i, j)]);
+                qs[(i * N + j) * HT_SLOTS] = q;
+                qs[(j * N + i) * HT_SLOTS] = q;
+                const float pw = __fadd_rn(__fadd_rn(a[i], a[j]), q);
+                const float mw = __fmul_rn(pw, rsqrt_approx(pw));
+                const float dw = fmaf(mw, P.inv_sigma_W, c_w);
+                const float cw = __fmul_rn(dw, dw);
+                const int p = j * (j - 1) / 2 + i;
+                if (cw < cap) {
+                    if (p < 64) mlo |= 1ull << p;
+                    else mhi |= 1u << (p - 64);
+                }
+            }
+        static_assert(NP <= 96, "pair mask");
+        *cands += (unsigned)((__popcll(mlo) + __popc(mhi)) * (N - 2));
+        float c1 = cap, c2 = cap, bm2 = 0.0f, bmw = 0.0f;
+        while (mlo | (unsigned long long)mhi) {
+            int p;
+            if (mlo) {
+                p = __ffsll((long long)mlo) - 1;
+                mlo &= mlo - 1ull;
+            } else {
+                p = 64 + __ffs(mhi) - 1;
+                mhi &= mhi - 1u;
+            }
+            const int code = pair_code[p];
+            const int i = code & 15, j = code >> 4;
+            const float pw = __fadd_rn(__fadd_rn(as[i * HT_SLOTS], as[j * HT_SLOTS]), qs[(i * N + j) * HT_SLOTS]);
+            const float mw = __fmul_rn(pw, rsqrt_approx(pw));
+            const float dw = fmaf(mw, P.inv_sigma_W, c_w);
+            const float cw = __fmul_rn(dw, dw);
+            const float* qi = qs + i * N * HT_SLOTS;
+            const float* qj = qs + j * N * HT_SLOTS;
+            const float before = c1;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const float m2 = __fadd_rn(__fadd_rn(__fadd_rn(pw, a[k]), qi[k * HT_SLOTS]), qj[k * HT_SLOTS]);
+                const float mt = __fmul_rn(m2, rsqrt_approx(m2));
+                const float dt = fmaf(mt, P.inv_sigma_t, c_t);
+                const float c = fmaf(dt, dt, cw);
+                bm2 = c < c1 ? m2 : bm2;
+                c2 = fminf(c2, fmaxf(c1, c));
+                c1 = fminf(c1, c);
+            }
+            bmw = c1 < before ? mw : bmw;
+        }
+        b1 = c1;
+        b2 = c2;
+        if (c1 < cap) {
+            mt_b = __fmul_rn(bm2, rsqrt_approx(bm2));
+            mw_b = bmw;
+        }
+    }
+}
+
+// Table of the pair codes i | j << 4 in pair-index order (p = j (j - 1) / 2 + i).
+__device__ __forceinline__ void fill_pair_codes(uint8_t* t)
+{
+    for (int p = threadIdx.x; p < npairs(MAX_JETS); p += blockDim.x) {
+        int j = 1;
+        while ((j + 1) * j / 2 <= p) ++j;
+        const int i = p - j * (j - 1) / 2;
+        t[p] = (uint8_t)(i | j << 4);
+    }
+}
+
 // ------------------------------------------------------------------ full Eq. 1 fit
 // Result of the full semileptonic fit of a unit (FP64, the definition's).
 struct FullFitD {
@@ -403,11 +518,10 @@ static __device__ __noinline__ float w_pz_fp64(const Plan& P, float4 l, float2 m
     double mx = met.x, my = met.y;
     if (P.smear_met || P.smear_jets) {
         uint4 w = philox4x32_10(ctr_of(3, v, event_id), key_of(seed));
-        double u0 = u01d(w.x), u1 = u01d(w.y);
-        double r = sqrt(-2.0 * log(u0));
-        double th = (2.0 * 3.141592653589793) * u1;
-        mx = (double)met.x + P.dsigma_met * (r * cos(th));
-        my = (double)met.y + P.dsigma_met * (r * sin(th));
+        double z12, z13;
+        box_muller_d(w.x, w.y, z12, z13);
+        mx = (double)met.x + P.dsigma_met * z12;
+        my = (double)met.y + P.dsigma_met * z13;
     }
     double lep[4] = {l.x, l.y, l.z, l.w};
     double pz;
@@ -446,6 +560,45 @@ struct CutStats {
     unsigned long long cands;  // triplet candidates evaluated in the block
 };
 
+// FP32 jet scales s_i = 1 + sigma_jet z_i of unit (event, v): normals z_0..z_11
+// from Philox blocks 0..2 (Box-Muller pairs (z_0, z_1), (z_2, z_3), ... of
+// each block); only the first N are formed.
+template <int N>
+__device__ __forceinline__ void jet_scales_f(const Plan& P, uint32_t v, uint64_t event_id, uint2 key,
+                                             float (&s)[N > 0 ? N : 1])
+{
+#pragma unroll
+    for (int b = 0; b < (N + 3) / 4; ++b) {
+        uint4 w = philox4x32_10(ctr_of(b, v, event_id), key);
+        float z0, z1, z2, z3;
+        box_muller_f(w.x, w.y, z0, z1);
+        if (4 * b + 0 < N) s[4 * b + 0] = fmaf(P.sigma_jet, z0, 1.0f);
+        if (4 * b + 1 < N) s[4 * b + 1] = fmaf(P.sigma_jet, z1, 1.0f);
+        if (4 * b + 2 < N) {
+            box_muller_f(w.z, w.w, z2, z3);
+            s[4 * b + 2] = fmaf(P.sigma_jet, z2, 1.0f);
+            if (4 * b + 3 < N) s[4 * b + 3] = fmaf(P.sigma_jet, z3, 1.0f);
+        }
+    }
+}
+
+// Modes of semi_unit_f.  UNIT_WHOLE evaluates everything in the unit's
+// thread.  UNIT_PROBE stops where the triplet chi2 is first needed and
+// returns f = F_NEED_TOP with the smeared MET state (mx, my, dmx, dmy) in
+// reco; the tile then evaluates the chi2 of all such units together and
+// completes them with UNIT_RESUME, which takes the MET state and the chi2
+// result from a TopIn instead of computing them.
+enum : int { UNIT_WHOLE = 0, UNIT_PROBE = 1, UNIT_RESUME = 2 };
+constexpr int F_NEED_TOP = -2;
+
+struct TopIn {
+    float4 met;        // smeared MET x, y and their error bounds
+    float b1, b2;      // clamped minimum and second minimum of the triplet chi2
+    float mt, mw;      // masses of the minimising candidate (when b1 < cap)
+    unsigned cyc;      // SM cycles of the chi2 evaluation
+    unsigned cands;    // candidates evaluated
+};
+
 // FP32 evaluation of one semileptonic unit.  exec: stage-2 cuts in execution
 // order.  After the first failure in execution order, the stage-2 cuts that
 // precede the earliest known failure in USER order and were not evaluated are
@@ -453,10 +606,11 @@ struct CutStats {
 // is the user-order one whatever the execution order.
 // F: the analysis has the full Eq. 1 fit (instantiated separately, so that the
 // triplet-only chain carries none of its code or registers).
-template <int N, bool F>
+template <int N, bool F, int MODE = UNIT_WHOLE>
 __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const SemiEvent<N>& ev,
-                               uint32_t v, uint64_t seed)
+                               uint32_t v, uint64_t seed, const TopIn* tin = nullptr)
 {
+    static_assert(MODE == UNIT_WHOLE || !F, "the split evaluation serves triplet-only analyses");
     UnitOut out;
     out.f = -1;
     out.reco = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -467,22 +621,13 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
     for (int i = 0; i < (N > 0 ? N : 1); ++i) s[i] = 1.0f;
     float mx = ev.met.x, my = ev.met.y, dmx = 0.0f, dmy = 0.0f;
     const uint2 key = key_of(seed);
-    if (P.smear_jets) {
-#pragma unroll
-        for (int b = 0; b < (N + 3) / 4; ++b) {
-            uint4 w = philox4x32_10(ctr_of(b, v, ev.event_id), key);
-            float z0, z1, z2, z3;
-            box_muller_f(w.x, w.y, z0, z1);
-            if (4 * b + 0 < N) s[4 * b + 0] = fmaf(P.sigma_jet, z0, 1.0f);
-            if (4 * b + 1 < N) s[4 * b + 1] = fmaf(P.sigma_jet, z1, 1.0f);
-            if (4 * b + 2 < N) {
-                box_muller_f(w.z, w.w, z2, z3);
-                s[4 * b + 2] = fmaf(P.sigma_jet, z2, 1.0f);
-                if (4 * b + 3 < N) s[4 * b + 3] = fmaf(P.sigma_jet, z3, 1.0f);
-            }
-        }
-    }
-    if (P.smear_met) {
+    if (MODE == UNIT_WHOLE && P.smear_jets) jet_scales_f<N>(P, v, ev.event_id, key, s);
+    if (MODE == UNIT_RESUME) {
+        mx = tin->met.x;
+        my = tin->met.y;
+        dmx = tin->met.z;
+        dmy = tin->met.w;
+    } else if (P.smear_met) {
         uint4 w = philox4x32_10(ctr_of(3, v, ev.event_id), key);
         float z12, z13;
         box_muller_f(w.x, w.y, z12, z13);
@@ -531,7 +676,20 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             unsure = fabsf(met - P.p0[c]) <= met_err;
         } else if (kind == CUT_HADTOP_CHI2_MAX) {
             if (!top_done) {
-                hadtop_f<N>(P, ev.g, s, chi2_cap(P, P.top_thr), b1, b2, mt_b, mw_b, &out.cands);
+                if constexpr (MODE == UNIT_PROBE) {
+                    out.f = F_NEED_TOP;
+                    out.reco = make_float4(mx, my, dmx, dmy);
+                    return out;
+                } else if constexpr (MODE == UNIT_RESUME) {
+                    b1 = tin->b1;
+                    b2 = tin->b2;
+                    mt_b = tin->mt;
+                    mw_b = tin->mw;
+                    out.cands += tin->cands;
+                    out.cyc_top += tin->cyc;
+                } else {
+                    hadtop_f<N>(P, ev.g, s, chi2_cap(P, P.top_thr), b1, b2, mt_b, mw_b, &out.cands);
+                }
                 top_done = true;
             }
             pass = b1 < P.p0[c];

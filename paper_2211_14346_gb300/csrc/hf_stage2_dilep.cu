@@ -233,11 +233,8 @@ __global__ void __launch_bounds__(BLOCK) k_bstage2_dilep(const BatchDev* __restr
 
 cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_bstage2_dilep, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    cudaError_t e = ensure_smem_attr((const void*)k_bstage2_dilep);
+    if (e != cudaSuccess) return e;
     int bs = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_dilep, BLOCK, smem);
     if (bs < 1) bs = 1;
@@ -249,11 +246,8 @@ cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Sc
                             uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
     const size_t smem = dl_smem_bytes(ept, ept * (int)V);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_stage2_dilep, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    cudaError_t e = ensure_smem_attr((const void*)k_stage2_dilep);
+    if (e != cudaSuccess) return e;
     int bs = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_dilep, BLOCK, smem);
     if (bs < 1) bs = 1;

@@ -6,10 +6,21 @@
 // variations.  Per tile: (A) the lepton and MET of its events are staged in
 // shared memory and each event's packed Gram matrix is computed once
 // (compensated FP32) from the jets in global memory, (B) every unit is
-// evaluated in FP32 registers (Philox smearing, MET cut, triplet chi2, W p_z)
-// with error bands, (C) one thread per event reduces its surviving units in
+// evaluated in FP32 (Philox smearing, MET cut, triplet chi2, W p_z) with
+// error bands, (C) one thread per event reduces its surviving units in
 // variation order and writes the event's outputs, or registers its flagged
 // units for the FP64 recheck.
+//
+// (B) for triplet-only analyses (N >= 3) runs in sub-batches of HT_UNITS
+// units and three steps: (B1) one thread per unit smears the MET and runs
+// the cut state machine up to the point where the triplet chi2 is needed
+// (UNIT_PROBE); those units are compacted into a list by warp ballot and a
+// prefix over the warp's lanes (one shared-memory atomic per warp); (B2) one
+// thread per listed unit smears the jets and evaluates the chi2 with the
+// smeared Gram terms in its own shared-memory column and the W pairs pruned
+// (hadtop_pruned), so every lane of a warp works on a unit that needs it,
+// and (B3) the same thread completes that unit (UNIT_RESUME) right away.  Analyses with
+// the full Eq. 1 fit, and N < 3, evaluate each unit whole in its thread.
 //
 // k_stage2_semi<N>: persistent grid over the tiles of one chunk.
 // k_bstage2_semi<N>: persistent grid over the tiles of every semileptonic
@@ -17,9 +28,97 @@
 // multiplicity, tile -> chunk by binary search in the per-chunk tile prefix).
 #pragma once
 #include "hf_common.cuh"
+#include "hf_kernels.h"
 #include "hf_semilep.cuh"
 
 namespace hf {
+
+// (B) of a tile of a triplet-only analysis: B1 probe, B2 chi2 of the listed
+// units, B3 completion, per sub-batch of HT_UNITS units.
+template <int N, class Grp>
+__device__ void semi_units_split(const Grp& g, const Plan& P, const Scratch& S, uint32_t V, uint64_t seed,
+                                 uint64_t first_id, int ne, TileSmem& sm, const int* exec, int nexec,
+                                 unsigned long long* fc, unsigned* hist, CutStats* st)
+{
+    const int r0 = g.rank(), gs = g.size();
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    constexpr int GST = gram_stride(N);
+    TopSmem ts = carve_top(sm.top, N);
+    const float cap = chi2_cap(P, P.top_thr);
+    const uint2 key = key_of(seed);
+    const int nu = ne * (int)V;
+    for (int u0 = 0; u0 < nu; u0 += HT_UNITS) {
+        const int u1 = min(nu, u0 + HT_UNITS);
+        if (r0 == 0) *ts.nh = 0;
+        if (u0 == 0) fill_pair_codes(ts.pair_code);
+        g.sync();
+        // B1: probe every unit; list the ones that need the chi2
+        for (int u = u0 + r0; u < u1; u += gs) {
+            const int ev = u / (int)V;
+            const uint32_t v = (uint32_t)(u - ev * (int)V);
+            SemiEvent<N> se;
+            se.g = sm.G + ev * GST;
+            se.jets = nullptr;
+            se.lep = sm.lep[ev];
+            se.met = sm.met[ev];
+            se.s1bits = sm.bits[ev];
+            se.event_id = first_id + sm.evid[ev];
+            UnitOut r = semi_unit_f<N, false, UNIT_PROBE>(P, exec, nexec, se, v, seed);
+            const bool need = r.f == F_NEED_TOP;
+            const unsigned am = __activemask();
+            const unsigned bal = __ballot_sync(am, need);
+            const unsigned leader = (unsigned)__ffs(am) - 1u;
+            unsigned base = 0;
+            if (lane == leader && bal) base = atomicAdd(ts.nh, (unsigned)__popc(bal));
+            base = __shfl_sync(am, base, leader);
+            if (need) {
+                const unsigned h = base + (unsigned)__popc(bal & lt);
+                ts.hidx[h] = (uint32_t)u;
+                ts.tin[h].met = r.reco;
+            } else {
+                sm.uf[u] = r.f;
+                sm.ureco[u] = r.reco;
+                warp_tally(P, r, fc, hist, st);
+            }
+        }
+        g.sync();
+        const int nh = (int)*ts.nh;
+        // B2 + B3: the chi2 of the listed units, one per thread, and at once the
+        // completion of the same unit (no block barrier between the two)
+        for (int h0 = 0; h0 < nh; h0 += gs) {
+            const int h = h0 + r0;
+            if (h < nh) {
+                const int u = (int)ts.hidx[h];
+                const int ev = u / (int)V;
+                const uint32_t v = (uint32_t)(u - ev * (int)V);
+                float s[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) s[i] = 1.0f;
+                if (P.smear_jets) jet_scales_f<N>(P, v, first_id + sm.evid[ev], key, s);
+                const long long t0 = clock64();
+                TopIn t;
+                t.met = ts.tin[h].met;
+                t.cands = 0;
+                hadtop_pruned<N>(P, sm.G + ev * GST, s, cap, ts.qs + r0, ts.as + r0, ts.pair_code, t.b1, t.b2, t.mt,
+                                 t.mw, &t.cands);
+                t.cyc = (unsigned)(clock64() - t0);
+                SemiEvent<N> se;
+                se.g = sm.G + ev * GST;
+                se.jets = nullptr;
+                se.lep = sm.lep[ev];
+                se.met = sm.met[ev];
+                se.s1bits = sm.bits[ev];
+                se.event_id = first_id + sm.evid[ev];
+                UnitOut r = semi_unit_f<N, false, UNIT_RESUME>(P, exec, nexec, se, v, seed, &t);
+                sm.uf[u] = r.f;
+                sm.ureco[u] = r.reco;
+                warp_tally(P, r, fc, hist, st);
+            }
+        }
+        g.sync();
+    }
+}
 
 template <int N, bool F, class Grp>
 __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
@@ -49,8 +148,11 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         }
     }
     g.sync();
-    // B: units
     const int nu = ne * (int)V;
+    if constexpr (!F && N >= 3) {
+        semi_units_split<N>(g, P, S, V, seed, first_id, ne, sm, exec, nexec, fc, hist, st);
+    } else {
+    // B: units
     for (int u = r0; u < nu; u += gs) {
         int ev = u / (int)V;
         uint32_t v = (uint32_t)(u - ev * (int)V);
@@ -66,10 +168,20 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         sm.ureco[u] = r.reco;
         warp_tally(P, r, fc, hist, st);
     }
+    }
     g.sync();
     // C: per-event reduction in variation order
     reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, fc, hist, r0, gs);
     g.sync();
+}
+
+// Blocks per SM the stage-2 kernels are compiled for (the register budget):
+// the shared memory of a triplet-only tile allows at most 2 blocks per SM
+// from 9 jets on and 3 at 7-8 jets (the smeared Gram terms of the chi2
+// step), so those get the registers of that occupancy.
+__host__ __device__ constexpr int s2_min_blocks(int n, bool full)
+{
+    return full ? (n >= 9 ? 3 : 4) : (n >= 9 ? 2 : n >= 7 ? 3 : 4);
 }
 
 // Block-level accumulators of the stage-2 kernels (shared memory).
@@ -108,7 +220,7 @@ struct S2Acc {
 // nearby code addresses of the (long, fully unrolled) unit evaluation, which
 // measured faster than independent per-warp tiles.
 template <int N, bool F>
-__global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
+__global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
                                                        int ev_per_tile)
 {
@@ -178,7 +290,7 @@ __device__ __forceinline__ void load_plan(Plan* dst, const Plan* src)
 // chunks [n_semi0, n_semi) (analyses with the full fit), each with its own
 // tile counter.
 template <int N, bool F>
-__global__ void __launch_bounds__(BLOCK, N >= 9 ? 3 : 4) k_bstage2_semi(const BatchDev* __restrict__ Bp)
+__global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_bstage2_semi(const BatchDev* __restrict__ Bp)
 {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ S2Acc acc;
@@ -245,12 +357,9 @@ template <int N, bool F>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
-    size_t smem = tile_smem_bytes(ept, ept * (int)V, gram_stride(N));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_stage2_semi<N, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    const size_t smem = semi_smem_bytes(N, F, ept, ept * (int)V);
+    cudaError_t e = ensure_smem_attr((const void*)k_stage2_semi<N, F>);
+    if (e != cudaSuccess) return e;
     int bs = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_semi<N, F>, BLOCK, smem);
     if (bs < 1) bs = 1;
@@ -262,11 +371,8 @@ cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scr
 template <int N, bool F>
 cudaError_t launch_bs2_semi(const BatchDev* B, size_t smem, int sms, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_bstage2_semi<N, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    cudaError_t e = ensure_smem_attr((const void*)k_bstage2_semi<N, F>);
+    if (e != cudaSuccess) return e;
     int bs = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_bstage2_semi<N, F>, BLOCK, smem);
     if (bs < 1) bs = 1;

@@ -135,6 +135,32 @@ def test_scheduler_reorders_without_changing_results(eng, orc):
     assert st["evaluated"][0] > 0
 
 
+def test_scheduler_with_eight_reorderable_cuts(eng, orc):
+    """Eight stage-2 cuts (four triplet chi2 thresholds before four MET
+    thresholds in the user order): beyond six cuts the scheduler scores the
+    user order, the greedy order by rank and its neighbours.  With the cut
+    flow completed in user order every unit must evaluate all cuts up to its
+    first user-order failure, so the user order is the cheapest and is kept;
+    every chunk equals the oracle."""
+    from paper_2211_14346_gb300 import DeviceColumns
+    cuts = [("hadtop_chi2_max", 40.0), ("hadtop_chi2_max", 30.0), ("hadtop_chi2_max", 20.0),
+            ("hadtop_chi2_max", 10.0), ("met_min", 10.0), ("met_min", 20.0), ("met_min", 30.0),
+            ("met_min", 40.0), ("njets_min", 4), ("wnu_solvable",)]
+    an = analyses.semilep(sigma_jet=0.1, sigma_met=10.0, cuts=cuts)
+    aid = eng.define(an)
+    for k in range(3):
+        cols = synth.gen_semilep(1500, 110 + k)
+        g = eng.run_device(aid, DeviceColumns(cols), V=8, seed=6, first_event_id=k * 10000).numpy()
+        o = orc.run(an, cols, seed=6, V=8, first_event_id=k * 10000)
+        assert_parity(g, o, what="chunk %d" % k)
+    st = eng.sched_state(aid)
+    order = st["order"].tolist()
+    assert sorted(order) == list(range(len(cuts)))
+    stage2 = [c for c in order if cuts[c][0] in ("hadtop_chi2_max", "met_min")]
+    assert stage2 == list(range(8)), order
+    assert (st["evaluated"][:8] > 0).all() and (st["cost"][:8] > 0).all()
+
+
 def test_async_submit_poll_fetch(eng, orc):
     """Host columns through hf_submit_chunk / hf_poll / hf_fetch_results with
     several chunks in flight (pinned and pageable host memory)."""
@@ -154,6 +180,28 @@ def test_async_submit_poll_fetch(eng, orc):
     with pytest.raises(Exception):
         eng.poll(tickets[0][0])
     assert HF_STATE_DONE == 2
+
+
+def test_fetch_timeout_keeps_the_ticket(eng):
+    """hf_fetch_results with timeout_ms = 0 on a ticket still running returns
+    HF_ETIMEOUT and keeps the ticket; a later fetch with a long timeout gets
+    the results, equal to the device-resident run of the same chunk."""
+    from paper_2211_14346_gb300 import PinnedColumns, DeviceColumns, HFError, _lib
+    an = analyses.config2()
+    aid = eng.define(an)
+    cols = synth.gen_semilep(1_000_000, 44)
+    h = PinnedColumns(cols)
+    t = eng.submit(aid, h, V=64, seed=23)
+    with pytest.raises(HFError) as ei:
+        eng.fetch(aid, t, cols.n_events, timeout_ms=0)
+    assert ei.value.status == _lib.HF_ETIMEOUT
+    assert eng.poll(t) in (0, 1, 2)  # the ticket is still known
+    g = eng.fetch(aid, t, cols.n_events, timeout_ms=600000)
+    ref = eng.run_device(aid, DeviceColumns(cols), V=64, seed=23).numpy()
+    assert np.array_equal(g["cutflow"], ref["cutflow"])
+    assert np.array_equal(g["mask"], ref["mask"])
+    with pytest.raises(HFError):
+        eng.poll(t)  # released by the successful fetch
 
 
 def test_malformed_columns_are_rejected(eng):
