@@ -248,11 +248,16 @@ def run_ours(a):
         cpu_base = cpu_oracle_throughput(a.cpu_seconds)  # before any CUDA call
     import numpy as np
     import torch
+    ndev = torch.cuda.device_count()
+    local = local % max(1, ndev)  # more ranks than GPUs (a test of the multi-rank path) share devices
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if world <= ndev:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:  # NCCL needs one GPU per rank; ranks sharing a GPU merge over gloo
+            dist.init_process_group("gloo")
     import synth
     from synth import analyses
     from paper_2211_14346_gb300 import build as hbuild
@@ -297,9 +302,10 @@ def run_ours(a):
     if dist is not None:  # the path's one exchange: exact integer sums of the shards' counts
         from paper_2211_14346_gb300.shard import merge_results
         merged = merge_results(dict(cutflow=res["cutflow"], hist=res["hist"], recheck_count=res["recheck_count"]),
-                               device="cuda")
+                               device="cuda" if dist.get_backend() == "nccl" else "cpu")
         res["cutflow"], res["hist"], res["recheck_count"] = merged["cutflow"], merged["hist"], merged["recheck_count"]
-    t = torch.tensor([ms], device="cuda")
+    mdev = "cuda" if dist is None or dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], device=mdev)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
@@ -375,7 +381,7 @@ def run_ours(a):
             eng.fetch(aid, tickets.pop(0), N, fields=fields, out=host_out)
         barrier()
         wall = time.perf_counter() - t_start
-        tw = torch.tensor([wall], device="cuda")
+        tw = torch.tensor([wall], device=mdev)
         if dist is not None:
             dist.all_reduce(tw, op=dist.ReduceOp.MAX)
         wall = float(tw.item())

@@ -76,9 +76,12 @@ typedef struct {
     void* stream;              /* optional cudaStream_t to order work after (NULL = own) */
 } hf_config;
 
-/* Opens a context on cfg->device.  cfg may be NULL (device 0, defaults).
- * *out receives the context; release it with hf_close.
- * Errors: HF_EINVAL (bad device), HF_ECUDA, HF_ENOMEM. */
+/* Opens a context on cfg->device: the state an analysis run needs on one
+ * GPU -- registered analyses, their cut schedulers, scratch memory, streams
+ * and in-flight chunks (the role of HEP-Frame's generated analysis skeleton
+ * and its run-time thread pool, Sect. 2 and Sect. 5.1, here for one device).
+ * cfg may be NULL (device 0, defaults).  *out receives the context; release
+ * it with hf_close.  Errors: HF_EINVAL (bad device), HF_ECUDA, HF_ENOMEM. */
 hf_status hf_open(const hf_config* cfg, hf_ctx** out);
 
 /* Closes the context: waits (bounded, 60 s) for in-flight work, frees all
@@ -137,6 +140,10 @@ typedef struct {
                                events that pass cuts 0..k (user order) in at least one
                                variation; 0 = no recording; bits >= n_cuts are invalid  */
     uint32_t record_vars[4]; /* HF_VAR_* stored in hf_record.value[0..3]               */
+    float sigma_lep;     /* relative lepton-energy resolution of the smearing, [0, 0.15]:
+                            lepton l of a unit is scaled by 1 + sigma_lep z[14 + l] (Sect. 4:
+                            every measured object is smeared); with sigma_lep != 0 the lepton
+                            pT cut and the W-mass solvability are decided per unit           */
 } hf_analysis_desc;
 
 /* Variables of the per-cut recording.  A variable is stored at every
@@ -194,7 +201,10 @@ typedef struct {
     uint64_t* n_records; /* 1 (device): records produced (may exceed record_cap)         */
 } hf_results;
 
-/* Asynchronous chunk submission (the serving entry point).  Admission: the
+/* Asynchronous chunk submission (the serving entry point): a chunk of events
+ * read by the caller enters the pipeline while earlier chunks are processed
+ * (Sect. 5.1: input reading and event processing run simultaneously; the
+ * events of a chunk are independent and processed in parallel).  Admission: the
  * chunk's device bytes (columns, results and cut-flow state, which stay
  * device-resident until fetched) must fit the context's HBM budget next to
  * the chunks in flight, else HF_EBUSY (nothing enqueued; retry after a fetch).
@@ -219,10 +229,13 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
 #define HF_STATE_DONE 2
 #define HF_STATE_FAILED 3
 
-/* Non-blocking state query of a ticket.  Errors: HF_ENOTFOUND. */
+/* Non-blocking state query of a ticket (the chunk's place in the pipeline of
+ * Sect. 5.1).  Errors: HF_ENOTFOUND. */
 hf_status hf_poll(hf_ctx* ctx, uint64_t ticket, int32_t* state);
 
-/* Waits (bounded by timeout_ms; 0 = poll once) for the ticket, then copies its
+/* The outputs of a chunk (Sect. 3: the selected events, the per-cut counts
+ * and the user's histograms; Appendix I: histogram filling).  Waits (bounded
+ * by timeout_ms; 0 = poll once) for the ticket, then copies its
  * results into the caller's HOST buffers of `out` (NULL fields skipped) and
  * releases the ticket.  Errors: HF_ETIMEOUT (ticket kept), HF_ENOTFOUND,
  * HF_EINVAL (device found malformed columns; ticket released), HF_ECUDA. */

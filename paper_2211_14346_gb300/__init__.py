@@ -183,8 +183,6 @@ class DeviceResults:
 def analysis_desc(an):
     """hf_analysis_desc of a user-level analysis dict (see synth.analyses);
     returns (desc, cuts): keep cuts alive while desc is in use."""
-    if float(an.get("sigma_lep", 0.0)) != 0.0:
-        raise ValueError("lepton smearing (sigma_lep) is not implemented by the CUDA path")
     cuts = _cut_struct(an["cuts"])
     d = _lib.hf_analysis_desc()
     d.event_model = _lib.HF_MODEL_SEMILEP if an["model"] == "semilep" else _lib.HF_MODEL_DILEP
@@ -192,6 +190,7 @@ def analysis_desc(an):
     d.cuts = C.cast(cuts, C.POINTER(_lib.hf_cut))
     for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
         setattr(d, k, _f32(an[k]))
+    d.sigma_lep = _f32(an.get("sigma_lep", 0.0))
     nb, lo, hi = an["hist"]
     d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
     rec = an.get("record")

@@ -56,7 +56,7 @@ class hf_analysis_desc(C.Structure):
                 ("mW", C.c_float), ("mt", C.c_float), ("sigma_t", C.c_float), ("sigma_W", C.c_float),
                 ("mH", C.c_float), ("sigma_jet", C.c_float), ("sigma_met", C.c_float),
                 ("hist_nbins", C.c_uint32), ("hist_lo", C.c_float), ("hist_hi", C.c_float),
-                ("record_levels", C.c_uint32), ("record_vars", C.c_uint32 * 4)]
+                ("record_levels", C.c_uint32), ("record_vars", C.c_uint32 * 4), ("sigma_lep", C.c_float)]
 
 
 class hf_columns(C.Structure):

@@ -298,6 +298,7 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     if (!(d->sigma_jet >= 0.0f && d->sigma_jet <= 0.15f))
         return fail(HF_EINVAL, "sigma_jet must be in [0, 0.15] (jet scale factors stay positive)");
     if (!(d->sigma_met >= 0.0f) || !std::isfinite(d->sigma_met)) return fail(HF_EINVAL, "sigma_met must be >= 0");
+    if (!(d->sigma_lep >= 0.0f && d->sigma_lep <= 0.15f)) return fail(HF_EINVAL, "sigma_lep must be in [0, 0.15]");
     if (d->hist_nbins < 1 || d->hist_nbins > (uint32_t)MAX_BINS || !(d->hist_lo < d->hist_hi))
         return fail(HF_EINVAL, "histogram: 1..1024 bins and lo < hi");
     if (d->record_levels >> d->n_cuts) return fail(HF_EINVAL, "record_levels names a cut level >= n_cuts");
@@ -354,6 +355,9 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     P.sigma_met = d->sigma_met;
     P.smear_jets = d->sigma_jet != 0.0f;
     P.smear_met = d->sigma_met != 0.0f;
+    P.sigma_lep = d->sigma_lep;
+    P.smear_lep = d->sigma_lep != 0.0f;
+    P.dsigma_lep = d->sigma_lep;
     P.nbins = (int)d->hist_nbins;
     P.lo = d->hist_lo;
     P.hi = d->hist_hi;
@@ -386,8 +390,10 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     P.stage2 = 0;
     for (int c = 0; c < P.n_cuts; ++c) {
         int k = P.kind[c];
-        bool s1 = k == CUT_NJETS_MIN || k == CUT_NBTAG_MIN || k == CUT_LEP_PT_MIN || k == CUT_LEP_OS ||
-                  k == CUT_W_NU_SOLVABLE || (k == CUT_MET_MIN && !P.smear_met);
+        // a smeared lepton moves its pT cut and the W-mass solvability to the units
+        bool s1 = k == CUT_NJETS_MIN || k == CUT_NBTAG_MIN || k == CUT_LEP_OS ||
+                  ((k == CUT_LEP_PT_MIN || k == CUT_W_NU_SOLVABLE) && !P.smear_lep) ||
+                  (k == CUT_MET_MIN && !P.smear_met);
         if (s1) P.stage1 |= 1u << c;
         else P.stage2 |= 1u << c;
     }
@@ -1566,6 +1572,7 @@ extern "C" hf_status hf_run_hl(hf_ctx* ctx, const hf_hl_desc* d, const hf_hl_col
     H.mll_min = d->mll_min;
     H.mtw_min = d->mtw_min;
     H.dr2 = (float)((double)d->dr_iso * (double)d->dr_iso);
+    H.dr_iso = d->dr_iso;
     H.dmet_min = d->met_min;
     H.dmll_min = d->mll_min;
     H.dmtw_min = d->mtw_min;

@@ -286,11 +286,8 @@ static __device__ __noinline__ int dilep_unit_fp64(const Plan& P, const Cols& C,
 {
     const float2 mf = C.met[e];
     double l1[4], l2[4];
-    {
-        float4 a = C.lep[2 * (uint64_t)e], b = C.lep[2 * (uint64_t)e + 1];
-        l1[0] = a.x; l1[1] = a.y; l1[2] = a.z; l1[3] = a.w;
-        l2[0] = b.x; l2[1] = b.y; l2[2] = b.z; l2[3] = b.w;
-    }
+    U.lepton(0, C.lep[2 * (uint64_t)e], l1);
+    U.lepton(1, C.lep[2 * (uint64_t)e + 1], l2);
     const unsigned btag = C.btag[e];
     bool done = false;
     DilepResD r;
@@ -303,6 +300,12 @@ static __device__ __noinline__ int dilep_unit_fp64(const Plan& P, const Cols& C,
         } else if (P.kind[c] == CUT_MET_MIN) {
             U.met(mf);
             pass = sqrt(U.metx * U.metx + U.mety * U.mety) > P.dp0[c];
+        } else if (P.kind[c] == CUT_LEP_PT_MIN) {
+            pass = sqrt(l1[0] * l1[0] + l1[1] * l1[1]) > P.dp0[c];
+        } else if (P.kind[c] == CUT_W_NU_SOLVABLE) {
+            U.met(mf);
+            double pz;
+            pass = w_pz_d(l1, U.metx, U.mety, P.dmW, &pz) != 0;
         } else {
             if (!done) {
                 U.met(mf);
@@ -343,13 +346,7 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
     double chi2 = 0.0, mtop = 0.0, mw = 0.0;
     FullFitD ff;
     double lep[4];
-    {
-        const float4 lf = C.lep[e];
-        lep[0] = lf.x;
-        lep[1] = lf.y;
-        lep[2] = lf.z;
-        lep[3] = lf.w;
-    }
+    U.lepton(0, C.lep[e], lep);
     int f = P.n_cuts;
     for (int c = 0; c < P.n_cuts; ++c) {
         bool pass;
@@ -358,6 +355,12 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         } else if (P.kind[c] == CUT_MET_MIN) {
             U.met(mf);
             pass = sqrt(U.metx * U.metx + U.mety * U.mety) > P.dp0[c];
+        } else if (P.kind[c] == CUT_LEP_PT_MIN) {
+            pass = sqrt(lep[0] * lep[0] + lep[1] * lep[1]) > P.dp0[c];
+        } else if (P.kind[c] == CUT_W_NU_SOLVABLE) {
+            U.met(mf);
+            double pz;
+            pass = w_pz_d(lep, U.metx, U.mety, P.dmW, &pz) != 0;
         } else if (P.kind[c] == CUT_HADTOP_CHI2_MAX) {
             if (!top_done) {
                 chi2 = hadtop_screened_d(P, U, &mtop, &mw);
@@ -653,7 +656,7 @@ __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsi
         if (leader && ne) {
             atomicAdd(&st->evaluated[c], ne);
             atomicAdd(&st->passed[c], np);
-            atomicAdd(&st->cost[c], (unsigned long long)(P.kind[c] == CUT_MET_MIN ? cm : ct));
+            atomicAdd(&st->cost[c], (unsigned long long)(heavy_cut(P.kind[c]) ? ct : cm));
         }
     }
 }
@@ -910,6 +913,10 @@ __host__ __device__ constexpr size_t top_smem_bytes(int n)
 {
     return n >= 3 ? (size_t)HT_UNITS * (sizeof(TopIn) + 4) + (size_t)(n * n + n) * HT_SLOTS * 4 + 128 : 0;
 }
+
+// Byte offset of the Gram-term columns (qs) in the chi2 step's region; the
+// stage-2 tile uses that space to stage its events' jets before the chi2 step.
+__host__ __device__ constexpr size_t top_qs_offset() { return (size_t)HT_UNITS * sizeof(TopIn); }
 
 __device__ inline TopSmem carve_top(char* p, int n)
 {

@@ -56,8 +56,8 @@ struct Plan {
     float top_thr;     // largest threshold of the chi2 cuts (clamp of the triplet minimum)
     int has_full;      // the analysis has a full Eq. 1 fit cut: it supplies the reco and histogram
     float mW2half, mW2half_lo;  // mW*mW/2 (exact in FP64) as a float-float pair
-    float sigma_jet, sigma_met;
-    int smear_jets, smear_met;
+    float sigma_jet, sigma_met, sigma_lep;
+    int smear_jets, smear_met, smear_lep;
     int nbins;
     float lo, hi, w;   // histogram
     // FP32 error model (relative / absolute bounds vs the FP64 definition)
@@ -67,7 +67,7 @@ struct Plan {
     float safety;      // multiplier on every band
     float pz_tol;      // relative accuracy demanded of p_z before recheck
     // the same in double for the FP64 path
-    double dmW, dmt, dsigma_t, dsigma_W, dmH, dsigma_jet, dsigma_met;
+    double dmW, dmt, dsigma_t, dsigma_W, dmH, dsigma_jet, dsigma_met, dsigma_lep;
     double dp0[MAX_CUTS], dp1[MAX_CUTS];
     double dlo, dhi;
     unsigned rec_levels; // per-cut recording: bit k records events passing cuts 0..k
@@ -143,6 +143,7 @@ struct Scratch {
 // the FP64 definition, in double (the same values).
 struct HLPlan {
     float met_min, mll_min, mtw_min, dr2;   // dr2 = dr_iso^2 (FP32)
+    float dr_iso;
     double dmet_min, dmll_min, dmtw_min, ddr_iso;
     double deta[3];                         // region boundaries of |eta|
     float sh[3];                            // sinh of the boundaries, rounded to FP32

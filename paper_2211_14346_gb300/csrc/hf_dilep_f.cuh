@@ -377,7 +377,7 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
     out.bin = 0;
     out.evald = out.passd = out.cyc_top = out.cyc_met = out.cands = 0;
     const unsigned bm = btag & ((1u << n) - 1u);
-    const bool smear = P.smear_jets || P.smear_met;
+    const bool smear = P.smear_jets || P.smear_met || P.smear_lep;
     double z[16];
     unsigned zdone = 0;
     auto pair = [&](int k) {  // FP64 smearing normals z[2k], z[2k+1]
@@ -406,8 +406,16 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
         mxd = (double)metf.x + P.dsigma_met * z[12];
         myd = (double)metf.y + P.dsigma_met * z[13];
     }
-    const double l1[4] = {lf1.x, lf1.y, lf1.z, lf1.w};
-    const double l2[4] = {lf2.x, lf2.y, lf2.z, lf2.w};
+    double l1[4] = {lf1.x, lf1.y, lf1.z, lf1.w};
+    double l2[4] = {lf2.x, lf2.y, lf2.z, lf2.w};
+    if (smear) {  // lepton l scaled by 1 + sigma_lep z[14 + l] (exactly 1 without lepton smearing)
+        pair(7);
+        const double s1 = 1.0 + P.dsigma_lep * z[14], s2 = 1.0 + P.dsigma_lep * z[15];
+        for (int k = 0; k < 4; ++k) {
+            l1[k] = s1 * l1[k];
+            l2[k] = s2 * l2[k];
+        }
+    }
     DilepRecoF reco;
     bool reco_done = false;
     unsigned evald = 0, passd = 0;
@@ -442,6 +450,13 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
             const double met = sqrt(mxd * mxd + myd * myd);
             pass = met > P.dp0[c];
             unsure = fabs(met - P.dp0[c]) <= 1.0e-9 * P.dp0[c];
+        } else if (kind == CUT_LEP_PT_MIN) {
+            const double pt = sqrt(l1[0] * l1[0] + l1[1] * l1[1]);
+            pass = pt > P.dp0[c];
+            unsure = fabs(pt - P.dp0[c]) <= 1.0e-9 * P.dp0[c];
+        } else if (kind == CUT_W_NU_SOLVABLE) {
+            double pz;
+            pass = w_pz_d(l1, mxd, myd, P.dmW, &pz) != 0;  // the definition's FP64 arithmetic
         } else {
             if (!reco_done) {
                 reco = dilep_reco_mixed(P, n, btag, jd, l1, l2, mxd, myd);
@@ -461,8 +476,8 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
             }
         }
         const unsigned dt = (unsigned)(clock64() - t0);
-        if (kind == CUT_MET_MIN) out.cyc_met += dt;
-        else out.cyc_top += dt;
+        if (heavy_cut(kind)) out.cyc_top += dt;
+        else out.cyc_met += dt;
         evald |= 1u << c;
         if (pass) passd |= 1u << c;
         out.evald = evald;

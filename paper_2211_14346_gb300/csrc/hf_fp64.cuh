@@ -285,7 +285,7 @@ struct LazyUnitD {
         j0 = C_.jet_off[e];
         n = (int)(C_.jet_off[e + 1] - j0);
         jp = C_.jets + j0;
-        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
+        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0 || P_.dsigma_lep != 0.0;
         zdone = jdone = 0;
         metdone = false;
     }
@@ -300,7 +300,7 @@ struct LazyUnitD {
         j0 = 0;
         n = n_;
         jp = jets;
-        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0;
+        smear = P_.dsigma_jet != 0.0 || P_.dsigma_met != 0.0 || P_.dsigma_lep != 0.0;
         zdone = jdone = 0;
         metdone = false;
     }
@@ -327,6 +327,19 @@ struct LazyUnitD {
             }
         }
         return jet[i];
+    }
+    // Lepton l of the unit: scaled by 1 + sigma_lep z[14 + l] (exactly 1 when
+    // sigma_lep = 0, as in the definition).
+    __device__ void lepton(int l, float4 lf, double* out)
+    {
+        const double c[4] = {lf.x, lf.y, lf.z, lf.w};
+        if (smear) {
+            pair(7);
+            const double s = 1.0 + P->dsigma_lep * z[14 + l];
+            for (int k = 0; k < 4; ++k) out[k] = s * c[k];
+        } else {
+            for (int k = 0; k < 4; ++k) out[k] = c[k];
+        }
     }
     __device__ void met(float2 mf)
     {

@@ -42,7 +42,7 @@ namespace hf {
 namespace {
 
 constexpr int HL_TILE = 256;    // events per tile (one per thread)
-constexpr int HL_JCAP = 1536;   // jets of a tile staged in shared memory (else read from global memory)
+constexpr int HL_JCAP = 1280;   // jets of a tile staged in shared memory (else read from global memory)
 constexpr int HL_LCAP = 512;    // leptons of a tile staged in shared memory
 constexpr unsigned HL_WAIT_LIMIT = 1u << 24;  // bounded waits on the copies
 
@@ -169,14 +169,19 @@ __device__ __forceinline__ bool eta_f(float4 p, float& eta)
 // Isolation of a lepton from one jet: FP32 Delta R^2 against dr_iso^2 with an
 // absolute band of 1e-4 (the FP32 Delta eta and Delta phi are within about
 // 2e-6 of the FP64 ones near the threshold), the FP64 definition inside it.
+// Two cheap certain cases come first: |Delta eta| beyond dr_iso (by more than
+// the eta error) and, for dr_iso < pi/2, transverse momenta more than 90
+// degrees apart (a negative dot product beyond its rounding bound).
 __device__ __forceinline__ bool isolated_from(const HLPlan& H, float4 l, float el, bool lok, float4 j, float ej,
                                               bool jok)
 {
     if (!lok || !jok) return isolated_from_d(H, l, j);
     const float de = __fsub_rn(el, ej);
+    if (fabsf(de) > H.dr_iso + 1.0e-5f) return true;
+    const float dt = fmaf(l.x, j.x, __fmul_rn(l.y, j.y));
+    if (H.dr_iso < 1.5f && dt < -2.4e-7f * (fabsf(l.x * j.x) + fabsf(l.y * j.y))) return true;
     // azimuth difference from the transverse cross and dot products
     const float cr = fmaf(l.x, j.y, -__fmul_rn(l.y, j.x));
-    const float dt = fmaf(l.x, j.x, __fmul_rn(l.y, j.y));
     const float dphi = atan2f(cr, dt);
     const float dr2 = fmaf(de, de, __fmul_rn(dphi, dphi));
     if (fabsf(dr2 - H.dr2) <= 1.0e-4f) return isolated_from_d(H, l, j);
@@ -324,6 +329,18 @@ struct HLSmem {
     uint32_t jbase[2], lbase[2];  // first jet / lepton of the staged tile
     uint32_t jcnt[2], lcnt[2];    // jets / leptons staged (0 when the tile reads global memory)
     unsigned long long counts[6];
+    // per tile (rewritten after each tile's last barrier)
+    uint16_t jev[HL_JCAP];        // tile-local event of each staged jet (0xffff: none)
+    uint8_t jk[HL_JCAP];          // its index within the event
+    uint16_t lev[HL_LCAP];        // tile-local event of each staged lepton
+    float leta[HL_LCAP];          // FP32 eta of each staged lepton
+    uint8_t lok[HL_LCAP];         // 1: leta valid (pT > 0)
+    unsigned cnt4[HL_TILE];       // per event: n1 | n2 << 8 | n3 << 16 | n_b << 24
+    unsigned iso[HL_TILE];        // per event: isolation bits of its leptons
+    uint16_t lofs[HL_TILE];       // per event: first staged lepton
+    uint16_t btag[HL_TILE];
+    uint8_t nlep[HL_TILE];
+    uint8_t mode[HL_TILE];        // 0: none or malformed, 1: staged, 2: read from global memory
     // followed by the per-channel histograms: unsigned [5][nbins + 2]
 };
 
@@ -345,8 +362,42 @@ __device__ __forceinline__ void stage_tile(const HLCols& C, uint32_t N, unsigned
     if (lb) bulk_g2s(sm.leps[s], C.lep + l0, lb, &sm.bar[s]);
 }
 
+// Jet counts per region, b-jets and isolation bits of one event by its own
+// thread (events whose records are not staged).
+__device__ inline void scan_event_direct(const HLPlan& H, const float4* jp, int n, const float4* lp, int nl,
+                                         unsigned bt, unsigned& c4, unsigned& iso)
+{
+    float el[HF_HL_MAX_LEPTONS];
+    bool lk[HF_HL_MAX_LEPTONS];
+    iso = 0;
+    for (int k = 0; k < nl; ++k) {
+        lk[k] = eta_f(lp[k], el[k]);
+        iso |= 1u << k;
+    }
+    c4 = 0;
+    for (int q = 0; q < n; ++q) {
+        const float4 j = jp[q];
+        const int g = region_f(H, j);
+        c4 += g == 1 ? 1u + ((bt >> q & 1u) << 24) : g == 2 ? 1u << 8 : g == 3 ? 1u << 16 : 0u;
+        if (iso) {
+            float ej = 0.0f;
+            const bool jok = eta_f(j, ej);
+            for (int k = 0; k < nl; ++k)
+                if ((iso >> k & 1u) && !isolated_from(H, lp[k], el[k], lk[k], j, ej, jok)) iso &= ~(1u << k);
+        }
+    }
+}
+
 }  // namespace
 
+// One tile in four steps separated by block barriers: (0) one thread per
+// event validates its offsets and maps its staged jets and leptons to it;
+// (1) one thread per staged lepton forms its eta; (2) one thread per staged
+// jet classifies its region, adds it to its event's packed counts and clears
+// the isolation bits of the event's leptons it is close to (shared-memory
+// atomics); (3) one thread per event takes the channel decisions, MET-
+// dependent ones per variation, and counts the units.  Steps 1-2 give every
+// lane the same amount of work whatever the events' multiplicities.
 __global__ void __launch_bounds__(HL_TILE) k_hl(const HLPlan H, const HLCols C, uint32_t N, uint32_t V, uint64_t seed,
                                                uint64_t first_id, HLOut O)
 {
@@ -368,117 +419,159 @@ __global__ void __launch_bounds__(HL_TILE) k_hl(const HLPlan H, const HLCols C, 
     unsigned long long cnt[6] = {0, 0, 0, 0, 0, 0};
     const uint2 key = key_of(seed);
     bool timed_out = false;
+    const int tid = threadIdx.x;
     for (unsigned i = 0; t < ntiles; ++i, t += gridDim.x) {
         const int s = (int)(i & 1u);
         const unsigned tn = t + gridDim.x;
-        if (threadIdx.x == 0 && tn < ntiles) stage_tile(C, N, tn, s ^ 1, sm);
-        if (!mbar_wait(&sm.bar[s], (i >> 1) & 1u)) {
-            timed_out = true;
-            break;
-        }
-        const uint32_t e = t * HL_TILE + threadIdx.x;
+        if (tid == 0 && tn < ntiles) stage_tile(C, N, tn, s ^ 1, sm);
+        const uint32_t jbase = sm.jbase[s], lbase = sm.lbase[s], jcnt = sm.jcnt[s], lcnt = sm.lcnt[s];
+        for (uint32_t j = tid; j < jcnt; j += HL_TILE) sm.jev[j] = 0xffffu;
+        for (uint32_t l = tid; l < lcnt; l += HL_TILE) sm.lev[l] = 0xffffu;
+        // (0) per event: validation and the maps of its staged records
+        const uint32_t e = t * HL_TILE + tid;
+        uint32_t j0 = 0, j1 = 0, l0 = 0, l1 = 0;
+        int md = 0;
         if (e < N) {
-            const uint32_t j0 = C.jet_off[e], j1 = C.jet_off[e + 1];
-            const uint32_t l0 = C.lep_off[e], l1 = C.lep_off[e + 1];
-            const int n = (int)(j1 - j0), nl = (int)(l1 - l0);
-            if (j1 < j0 || n > HF_HL_MAX_JETS || (uint64_t)j1 > C.n_jets || l1 < l0 || nl > HF_HL_MAX_LEPTONS ||
-                (uint64_t)l1 > C.n_leps) {
+            j0 = C.jet_off[e];
+            j1 = C.jet_off[e + 1];
+            l0 = C.lep_off[e];
+            l1 = C.lep_off[e + 1];
+            if (j1 < j0 || j1 - j0 > HF_HL_MAX_JETS || (uint64_t)j1 > C.n_jets || l1 < l0 ||
+                l1 - l0 > HF_HL_MAX_LEPTONS || (uint64_t)l1 > C.n_leps) {
                 atomicOr(O.err, ERR_COLUMNS);
                 if (O.channel)
                     for (uint32_t v = 0; v < V; ++v) O.channel[(uint64_t)e * V + v] = 0;
             } else {
-                // the staged records when the event's lie inside the staged range
-                // (always for well-formed offsets), else global memory
-                const bool js = j0 >= sm.jbase[s] && j1 - sm.jbase[s] <= sm.jcnt[s];
-                const bool ls = l0 >= sm.lbase[s] && l1 - sm.lbase[s] <= sm.lcnt[s];
-                const float4* jp = js ? sm.jets[s] + (j0 - sm.jbase[s]) : C.jets + j0;
-                const float4* lp = ls ? sm.leps[s] + (l0 - sm.lbase[s]) : C.lep + l0;
-                float4 leps[HF_HL_MAX_LEPTONS];
-                float el[HF_HL_MAX_LEPTONS];
-                bool lok[HF_HL_MAX_LEPTONS];
-                unsigned iso = 0;
-                for (int k = 0; k < nl; ++k) {
-                    leps[k] = lp[k];
-                    lok[k] = eta_f(leps[k], el[k]);
-                    iso |= 1u << k;
-                }
-                const unsigned bt = C.btag[e];
-                int n1 = 0, n2 = 0, n3 = 0, nbj = 0;
-                for (int q = 0; q < n; ++q) {
-                    const float4 j = jp[q];
-                    const int g = region_f(H, j);
-                    n1 += g == 1;
-                    n2 += g == 2;
-                    n3 += g == 3;
-                    nbj += g == 1 && (bt >> q & 1u);
-                    if (iso) {
-                        float ej = 0.0f;
-                        const bool jok = eta_f(j, ej);
-                        for (int k = 0; k < nl; ++k)
-                            if ((iso >> k & 1u) && !isolated_from(H, leps[k], el[k], lok[k], j, ej, jok))
-                                iso &= ~(1u << k);
-                    }
-                }
-                const int niso = __popc(iso);
-                // the signal channel this event can reach, before the MET-dependent requirements
-                int ch = 0;
-                int ia = -1;
-                bool need_mtw = false;
-                const bool clean = n2 == 0 && n3 == 0;
-                if (niso == 1) {
-                    ia = __ffs(iso) - 1;
-                    if (n1 >= 4 && nbj == 2 && clean) ch = 1;
-                    else if (n1 == 1 && n2 + n3 == 1 && nbj == 1) ch = 3;
-                    else if (n1 == 3 && nbj == 1 && clean) {
-                        ch = 4;
-                        need_mtw = true;
-                    }
-                } else if (niso == 2) {
-                    const int a = __ffs(iso) - 1;
-                    const int b = __ffs(iso & ~(1u << a)) - 1;
-                    const int la = (int)(l0 + a), lb = (int)(l0 + b);
-                    if (C.lep_q[la] * C.lep_q[lb] < 0 && C.lep_flav[la] != C.lep_flav[lb]) {
-                        if (n1 >= 2 && nbj == 2 && clean && mll_pass(H, leps[a], leps[b])) ch = 2;
-                        else if ((n1 == 1 || n1 == 2) && nbj == 1 && clean) ch = 5;
-                    }
-                }
-                const float2 m = C.met[e];
-                const uint64_t eid = first_id + e;
-                unsigned sig = 0;  // units in channel ch
-                if (ch == 0) {
-                    if (O.channel)
-                        for (uint32_t v = 0; v < V; ++v) O.channel[(uint64_t)e * V + v] = 0;
-                } else if (!H.smear) {
-                    float mx, my, dmx, dmy;
-                    met_f(H, m, eid, 0, key, mx, my, dmx, dmy);
-                    bool pass = met_pass(H, m, eid, 0, seed, mx, my, dmx, dmy);
-                    if (pass && need_mtw) pass = mtw_pass(H, leps[ia], m, eid, 0, seed, mx, my, dmx, dmy);
-                    sig = pass ? V : 0;
-                    if (O.channel)
-                        for (uint32_t v = 0; v < V; ++v) O.channel[(uint64_t)e * V + v] = (int8_t)(pass ? ch : 0);
-                } else {
-                    for (uint32_t v = 0; v < V; ++v) {
-                        float mx, my, dmx, dmy;
-                        met_f(H, m, eid, v, key, mx, my, dmx, dmy);
-                        bool pass = met_pass(H, m, eid, v, seed, mx, my, dmx, dmy);
-                        if (pass && need_mtw) pass = mtw_pass(H, leps[ia], m, eid, v, seed, mx, my, dmx, dmy);
-                        sig += pass;
-                        if (O.channel) O.channel[(uint64_t)e * V + v] = (int8_t)(pass ? ch : 0);
-                    }
-                }
-                cnt[0] += V - sig;
-                if (sig) {
-                    cnt[ch] += sig;
-                    atomicAdd(&s_hist[(ch - 1) * nb2 + lead_bin(H, leps, iso, nl)], sig);
-                }
+                const bool js = j0 >= jbase && j1 - jbase <= jcnt;
+                const bool ls = l0 >= lbase && l1 - lbase <= lcnt;
+                md = js && ls ? 1 : 2;
             }
         }
-        __syncthreads();  // every thread is done with stage s before it is refilled
+        __syncthreads();  // the maps are cleared
+        const int n = (int)(j1 - j0), nl = (int)(l1 - l0);
+        sm.mode[tid] = (uint8_t)md;
+        if (md == 1) {
+            sm.cnt4[tid] = 0;
+            sm.iso[tid] = (1u << nl) - 1u;
+            sm.lofs[tid] = (uint16_t)(l0 - lbase);
+            sm.nlep[tid] = (uint8_t)nl;
+            sm.btag[tid] = C.btag[e];
+            for (int q = 0; q < n; ++q) {
+                sm.jev[j0 - jbase + q] = (uint16_t)tid;
+                sm.jk[j0 - jbase + q] = (uint8_t)q;
+            }
+            for (int k = 0; k < nl; ++k) sm.lev[l0 - lbase + k] = (uint16_t)tid;
+        }
+        if (!mbar_wait(&sm.bar[s], (i >> 1) & 1u)) timed_out = true;
+        if (__syncthreads_or(timed_out)) {
+            timed_out = true;
+            break;
+        }
+        // (1) per staged lepton: eta
+        for (uint32_t l = tid; l < lcnt; l += HL_TILE) {
+            if (sm.lev[l] == 0xffffu) continue;
+            float el = 0.0f;
+            sm.lok[l] = eta_f(sm.leps[s][l], el) ? 1 : 0;
+            sm.leta[l] = el;
+        }
+        __syncthreads();
+        // (2) per staged jet: region, counts, isolation of its event's leptons
+        for (uint32_t j = tid; j < jcnt; j += HL_TILE) {
+            const unsigned ev = sm.jev[j];
+            if (ev == 0xffffu) continue;
+            const float4 jet = sm.jets[s][j];
+            const int g = region_f(H, jet);
+            const unsigned add = g == 1 ? 1u + ((unsigned)(sm.btag[ev] >> sm.jk[j] & 1u) << 24)
+                                        : g == 2 ? 1u << 8 : g == 3 ? 1u << 16 : 0u;
+            if (add) atomicAdd(&sm.cnt4[ev], add);
+            const int nle = sm.nlep[ev];
+            if (nle && sm.iso[ev]) {
+                float ej = 0.0f;
+                const bool jok = eta_f(jet, ej);
+                const int lo = sm.lofs[ev];
+                unsigned clear = 0;
+                for (int k = 0; k < nle; ++k)
+                    if (!isolated_from(H, sm.leps[s][lo + k], sm.leta[lo + k], sm.lok[lo + k] != 0, jet, ej, jok))
+                        clear |= 1u << k;
+                if (clear) atomicAnd(&sm.iso[ev], ~clear);
+            }
+        }
+        __syncthreads();
+        // (3) per event: channel decisions and counts
+        if (md) {
+            unsigned c4, iso;
+            const float4* lp;
+            if (md == 1) {
+                c4 = sm.cnt4[tid];
+                iso = sm.iso[tid];
+                lp = sm.leps[s] + (l0 - lbase);
+            } else {
+                lp = C.lep + l0;
+                scan_event_direct(H, C.jets + j0, n, lp, nl, C.btag[e], c4, iso);
+            }
+            const int n1 = (int)(c4 & 255u), n2 = (int)(c4 >> 8 & 255u), n3 = (int)(c4 >> 16 & 255u);
+            const int nbj = (int)(c4 >> 24);
+            const int niso = __popc(iso);
+            // the signal channel this event can reach, before the MET-dependent requirements
+            int ch = 0;
+            int ia = -1;
+            bool need_mtw = false;
+            const bool clean = n2 == 0 && n3 == 0;
+            if (niso == 1) {
+                ia = __ffs(iso) - 1;
+                if (n1 >= 4 && nbj == 2 && clean) ch = 1;
+                else if (n1 == 1 && n2 + n3 == 1 && nbj == 1) ch = 3;
+                else if (n1 == 3 && nbj == 1 && clean) {
+                    ch = 4;
+                    need_mtw = true;
+                }
+            } else if (niso == 2) {
+                const int a = __ffs(iso) - 1;
+                const int b = __ffs(iso & ~(1u << a)) - 1;
+                const uint32_t la = l0 + a, lb = l0 + b;
+                if (C.lep_q[la] * C.lep_q[lb] < 0 && C.lep_flav[la] != C.lep_flav[lb]) {
+                    if (n1 >= 2 && nbj == 2 && clean && mll_pass(H, lp[a], lp[b])) ch = 2;
+                    else if ((n1 == 1 || n1 == 2) && nbj == 1 && clean) ch = 5;
+                }
+            }
+            const float2 m = C.met[e];
+            const uint64_t eid = first_id + e;
+            unsigned sig = 0;  // units in channel ch
+            if (ch == 0) {
+                if (O.channel)
+                    for (uint32_t v = 0; v < V; ++v) O.channel[(uint64_t)e * V + v] = 0;
+            } else if (!H.smear) {
+                float mx, my, dmx, dmy;
+                met_f(H, m, eid, 0, key, mx, my, dmx, dmy);
+                bool pass = met_pass(H, m, eid, 0, seed, mx, my, dmx, dmy);
+                if (pass && need_mtw) pass = mtw_pass(H, lp[ia], m, eid, 0, seed, mx, my, dmx, dmy);
+                sig = pass ? V : 0;
+                if (O.channel)
+                    for (uint32_t v = 0; v < V; ++v) O.channel[(uint64_t)e * V + v] = (int8_t)(pass ? ch : 0);
+            } else {
+                for (uint32_t v = 0; v < V; ++v) {
+                    float mx, my, dmx, dmy;
+                    met_f(H, m, eid, v, key, mx, my, dmx, dmy);
+                    bool pass = met_pass(H, m, eid, v, seed, mx, my, dmx, dmy);
+                    if (pass && need_mtw) pass = mtw_pass(H, lp[ia], m, eid, v, seed, mx, my, dmx, dmy);
+                    sig += pass;
+                    if (O.channel) O.channel[(uint64_t)e * V + v] = (int8_t)(pass ? ch : 0);
+                }
+            }
+            cnt[0] += V - sig;
+            if (sig) {
+                cnt[ch] += sig;
+                float4 leps[HF_HL_MAX_LEPTONS];
+                for (int k = 0; k < nl; ++k) leps[k] = lp[k];
+                atomicAdd(&s_hist[(ch - 1) * nb2 + lead_bin(H, leps, iso, nl)], sig);
+            }
+        }
+        __syncthreads();  // every thread is done with stage s and the tile's maps
     }
     if (timed_out) {
         // a copy that never completed: record it and give the other stage a
         // bounded chance to land before the block's shared memory goes away
-        if (threadIdx.x == 0) atomicOr(O.err, ERR_TIMEOUT);
+        if (tid == 0) atomicOr(O.err, ERR_TIMEOUT);
         mbar_wait(&sm.bar[0], 0);
         mbar_wait(&sm.bar[1], 0);
         return;
@@ -487,11 +580,11 @@ __global__ void __launch_bounds__(HL_TILE) k_hl(const HLPlan H, const HLCols C, 
     for (int c = 0; c < 6; ++c) {
         unsigned long long x = cnt[c];
         for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31u) == 0 && x) atomicAdd(&sm.counts[c], x);
+        if ((tid & 31) == 0 && x) atomicAdd(&sm.counts[c], x);
     }
     __syncthreads();
-    if (threadIdx.x < 6 && sm.counts[threadIdx.x]) atomicAdd(&O.counts[threadIdx.x], sm.counts[threadIdx.x]);
-    for (int b = threadIdx.x; b < 5 * nb2; b += blockDim.x)
+    if (tid < 6 && sm.counts[tid]) atomicAdd(&O.counts[tid], sm.counts[tid]);
+    for (int b = tid; b < 5 * nb2; b += blockDim.x)
         if (s_hist[b]) atomicAdd(&O.hist[b], (unsigned long long)s_hist[b]);
 }
 

@@ -22,14 +22,22 @@
 
 namespace hf {
 
+// Cuts whose cost is a reconstruction (charged the unit's reconstruction
+// cycles in the scheduler statistics); the others are charged the cheap ones.
+__host__ __device__ constexpr bool heavy_cut(int kind)
+{
+    return kind == CUT_HADTOP_CHI2_MAX || kind == CUT_TTBAR_CHI2_MAX || kind == CUT_DILEP_SOLVABLE ||
+           kind == CUT_HIGGS_WINDOW;
+}
+
 struct UnitOut {
     int f;             // cuts passed in user order (n_cuts = survives); -1 = recheck
     float4 reco;       // (m_top, m_W, pz_nu, |MET|) when f == n_cuts
     int bin;           // histogram bin when f == n_cuts
     unsigned evald;    // stage-2 cuts evaluated (bit = user index)
     unsigned passd;    // stage-2 cuts passed
-    unsigned cyc_top;  // SM cycles spent in the triplet chi2
-    unsigned cyc_met;  // SM cycles spent in the MET cut
+    unsigned cyc_top;  // SM cycles spent in the reconstruction cuts (heavy_cut)
+    unsigned cyc_met;  // SM cycles spent in the other stage-2 cuts
     unsigned cands;    // triplet candidates evaluated (after pair pruning)
 };
 
@@ -516,14 +524,20 @@ static __device__ __noinline__ float w_pz_fp64(const Plan& P, float4 l, float2 m
                                         uint32_t v)
 {
     double mx = met.x, my = met.y;
-    if (P.smear_met || P.smear_jets) {
+    double lep[4] = {l.x, l.y, l.z, l.w};
+    if (P.smear_met || P.smear_jets || P.smear_lep) {
         uint4 w = philox4x32_10(ctr_of(3, v, event_id), key_of(seed));
         double z12, z13;
         box_muller_d(w.x, w.y, z12, z13);
         mx = (double)met.x + P.dsigma_met * z12;
         my = (double)met.y + P.dsigma_met * z13;
+        if (P.smear_lep) {
+            double z14, z15;
+            box_muller_d(w.z, w.w, z14, z15);
+            const double sl = 1.0 + P.dsigma_lep * z14;
+            for (int k = 0; k < 4; ++k) lep[k] = sl * lep[k];
+        }
     }
-    double lep[4] = {l.x, l.y, l.z, l.w};
     double pz;
     w_pz_d(lep, mx, my, P.dmW, &pz);
     return (float)pz;
@@ -548,7 +562,8 @@ __device__ __noinline__ FullFitD semi_full_fit(const Plan& P, const SemiEvent<N>
 {
     LazyUnitD U;
     U.init_jets(P, ev.jets, N, ev.event_id, seed, v);
-    const double lep[4] = {ev.lep.x, ev.lep.y, ev.lep.z, ev.lep.w};
+    double lep[4];
+    U.lepton(0, ev.lep, lep);
     return ttbar_screened(P, U, ev.g, s, lep, ev.met);
 }
 
@@ -622,20 +637,32 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
     float mx = ev.met.x, my = ev.met.y, dmx = 0.0f, dmy = 0.0f;
     const uint2 key = key_of(seed);
     if (MODE == UNIT_WHOLE && P.smear_jets) jet_scales_f<N>(P, v, ev.event_id, key, s);
+    // lepton scale s_l = 1 + sigma_lep z14 and its error bound (Philox block 3,
+    // words z, w; the MET shift uses words x, y of the same block)
+    float sl = 1.0f, dsl = 0.0f;
     if (MODE == UNIT_RESUME) {
         mx = tin->met.x;
         my = tin->met.y;
         dmx = tin->met.z;
         dmy = tin->met.w;
-    } else if (P.smear_met) {
+    }
+    if ((MODE != UNIT_RESUME && P.smear_met) || P.smear_lep) {
         uint4 w = philox4x32_10(ctr_of(3, v, ev.event_id), key);
-        float z12, z13;
-        box_muller_f(w.x, w.y, z12, z13);
-        mx = fmaf(P.sigma_met, z12, ev.met.x);
-        my = fmaf(P.sigma_met, z13, ev.met.y);
         const float u = 5.9604645e-8f;
-        dmx = P.sigma_met * P.z_rel * fabsf(z12) + u * fabsf(mx);
-        dmy = P.sigma_met * P.z_rel * fabsf(z13) + u * fabsf(my);
+        if (MODE != UNIT_RESUME && P.smear_met) {
+            float z12, z13;
+            box_muller_f(w.x, w.y, z12, z13);
+            mx = fmaf(P.sigma_met, z12, ev.met.x);
+            my = fmaf(P.sigma_met, z13, ev.met.y);
+            dmx = P.sigma_met * P.z_rel * fabsf(z12) + u * fabsf(mx);
+            dmy = P.sigma_met * P.z_rel * fabsf(z13) + u * fabsf(my);
+        }
+        if (P.smear_lep) {
+            float z14, z15;
+            box_muller_f(w.z, w.w, z14, z15);
+            sl = fmaf(P.sigma_lep, z14, 1.0f);
+            dsl = P.sigma_lep * P.z_rel * fabsf(z14) + u * sl;
+        }
     }
     float b1 = CUDART_INF_F, b2 = CUDART_INF_F, mt_b = 0.f, mw_b = 0.f;
     bool top_done = false;
@@ -674,6 +701,17 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             }
             pass = met > P.p0[c];
             unsure = fabsf(met - P.p0[c]) <= met_err;
+        } else if (kind == CUT_LEP_PT_MIN) {
+            // smeared lepton pT = s_l pT: FP32 with the bound of s_l and the rounding
+            const float pt = __fmul_rn(sqrtf(fmaf(ev.lep.x, ev.lep.x, __fmul_rn(ev.lep.y, ev.lep.y))), sl);
+            pass = pt > P.p0[c];
+            unsure = fabsf(pt - P.p0[c]) <= P.safety * (pt * (dsl / sl + 3.6e-7f));
+        } else if (kind == CUT_W_NU_SOLVABLE) {
+            // E^2 - pz^2 of the smeared lepton is s_l^2 (E^2 - pz^2): the FP32
+            // product (E - pz)(E + pz) has its exact sign; near 0 the FP64 one decides
+            const float a = __fmul_rn(__fsub_rn(ev.lep.w, ev.lep.z), __fadd_rn(ev.lep.w, ev.lep.z));
+            pass = a > 0.0f;
+            unsure = fabsf(a) <= 1.0e-6f * __fmul_rn(ev.lep.w, ev.lep.w);
         } else if (kind == CUT_HADTOP_CHI2_MAX) {
             if (!top_done) {
                 if constexpr (MODE == UNIT_PROBE) {
@@ -704,8 +742,8 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             }
         }
         const unsigned dt = (unsigned)(clock64() - t0);
-        if (kind == CUT_MET_MIN) out.cyc_met += dt;
-        else out.cyc_top += dt;
+        if (heavy_cut(kind)) out.cyc_top += dt;
+        else out.cyc_met += dt;
         evald |= 1u << c;
         if (pass) passd |= 1u << c;
         out.evald = evald;
@@ -729,7 +767,9 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         if (!top_done) return out;  // (the model always has the chi2 cut)
         if (b2 - b1 <= chi2_band(P, b1) + chi2_band(P, b2)) return out;  // argmin near-tie
         float pz;
-        if (!w_pz_f(P, ev.lep, mx, my, dmx, dmy, pz)) pz = w_pz_fp64(P, ev.lep, ev.met, seed, ev.event_id, v);
+        // with a smeared lepton the float-float bound does not cover the lepton's
+        // error: p_z (a reconstructed value, no decision) comes from FP64
+        if (P.smear_lep || !w_pz_f(P, ev.lep, mx, my, dmx, dmy, pz)) pz = w_pz_fp64(P, ev.lep, ev.met, seed, ev.event_id, v);
         if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
         bool hu = false;
         int bin = hist_bin_f(P, mt_b, P.safety * P.e_m * mt_b, &hu);

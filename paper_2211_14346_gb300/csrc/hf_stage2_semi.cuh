@@ -127,6 +127,38 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
 {
     const int r0 = g.rank(), gs = g.size();
     // A: stage lepton / MET, then the packed Gram matrices
+    constexpr int NT = ntri(N);
+    constexpr int GST = gram_stride(N);
+    if constexpr (!F && N >= 3) {
+        // the jets of the tile's events are first copied into the chi2 step's
+        // shared-memory region (free until then), every load independent of the
+        // others, so that the Gram terms wait for one round of global loads
+        // instead of one per entry
+        float4* sj = (float4*)(sm.top + top_qs_offset());
+        __shared__ uint32_t s_j0[MAX_EV_PER_TILE];
+        for (int t = r0; t < ne; t += gs) {
+            uint2 en = ents[t];
+            sm.evid[t] = en.x;
+            sm.bits[t] = en.y;
+            sm.lep[t] = __ldg(&C.lep[en.x]);
+            sm.met[t] = __ldg(&C.met[en.x]);
+            s_j0[t] = __ldg(&C.jet_off[en.x]);
+        }
+        g.sync();
+        for (int t = r0; t < ne * N; t += gs) {
+            const int ev = t / N, k = t - ev * N;
+            sj[t] = __ldg(&C.jets[s_j0[ev] + k]);
+        }
+        g.sync();
+        for (int t = r0; t < ne * NT; t += gs) {
+            int ev = t / NT, k = t - ev * NT;
+            int j = 0;
+            while ((j + 1) * (j + 2) / 2 <= k) ++j;
+            int i = k - j * (j + 1) / 2;
+            sm.G[ev * GST + k] = minkowski_dot2(sj[ev * N + i], sj[ev * N + j]);
+        }
+        g.sync();
+    } else {
     for (int t = r0; t < ne; t += gs) {
         uint2 en = ents[t];
         sm.evid[t] = en.x;
@@ -135,8 +167,6 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         sm.met[t] = __ldg(&C.met[en.x]);
     }
     g.sync();
-    constexpr int NT = ntri(N);
-    constexpr int GST = gram_stride(N);
     if constexpr (NT > 0) {
         for (int t = r0; t < ne * NT; t += gs) {
             int ev = t / NT, k = t - ev * NT;
@@ -148,6 +178,7 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         }
     }
     g.sync();
+    }
     const int nu = ne * (int)V;
     if constexpr (!F && N >= 3) {
         semi_units_split<N>(g, P, S, V, seed, first_id, ne, sm, exec, nexec, fc, hist, st);

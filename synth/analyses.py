@@ -7,6 +7,7 @@ An analysis is a dict:
     mW, mt, sigma_t, sigma_W, mH      physics constants (GeV)
     sigma_jet  relative jet-energy resolution of the smearing (0 = none)
     sigma_met  absolute MET resolution per component, GeV (0 = none)
+    sigma_lep  relative lepton-energy resolution (0 = none; optional key)
     hist       (nbins, lo, hi) of the reconstructed-mass histogram
 
 Both the C-ABI binding and the oracle binding marshal this dict into their
@@ -26,7 +27,7 @@ CUT_NAMES = ("njets_min", "nbtag_min", "lep_pt_min", "met_min", "wnu_solvable",
 
 
 def semilep(sigma_jet=0.0, sigma_met=0.0, sigma_t=15.0, sigma_W=10.0,
-            cuts=None):
+            cuts=None, sigma_lep=0.0):
     """Semileptonic chain C1..C6: >= 4 jets, >= 1 b-tag, lepton pT > 30,
     MET > 20, solvable W-mass neutrino p_z, best hadronic-top chi2 < 10;
     m_W = 80.4, m_t = 172.5, widths 15 / 10, m_top histogram 50 bins 0-500."""
@@ -35,10 +36,10 @@ def semilep(sigma_jet=0.0, sigma_met=0.0, sigma_t=15.0, sigma_W=10.0,
                 ("met_min", 20.0), ("wnu_solvable",), ("hadtop_chi2_max", 10.0)]
     return dict(model="semilep", cuts=list(cuts), mW=80.4, mt=172.5,
                 sigma_t=sigma_t, sigma_W=sigma_W, mH=125.0,
-                sigma_jet=sigma_jet, sigma_met=sigma_met, hist=(50, 0.0, 500.0))
+                sigma_jet=sigma_jet, sigma_met=sigma_met, sigma_lep=sigma_lep, hist=(50, 0.0, 500.0))
 
 
-def semilep_full(sigma_jet=0.0, sigma_met=0.0, sigma_t=11.5, sigma_W=7.5, cuts=None):
+def semilep_full(sigma_jet=0.0, sigma_met=0.0, sigma_t=11.5, sigma_W=7.5, cuts=None, sigma_lep=0.0):
     """Semileptonic chain with the full Eq. 1 fit (both tops, both W bosons,
     both neutrino solutions) in place of the hadronic-top cut: >= 4 jets,
     >= 1 b-tag, lepton pT > 30, MET > 20, solvable W-mass neutrino p_z,
@@ -49,10 +50,10 @@ def semilep_full(sigma_jet=0.0, sigma_met=0.0, sigma_t=11.5, sigma_W=7.5, cuts=N
                 ("met_min", 20.0), ("wnu_solvable",), ("ttbar_chi2_max", 20.0)]
     return dict(model="semilep", cuts=list(cuts), mW=80.4, mt=172.5,
                 sigma_t=sigma_t, sigma_W=sigma_W, mH=125.0,
-                sigma_jet=sigma_jet, sigma_met=sigma_met, hist=(50, 0.0, 500.0))
+                sigma_jet=sigma_jet, sigma_met=sigma_met, sigma_lep=sigma_lep, hist=(50, 0.0, 500.0))
 
 
-def dilep(sigma_jet=0.0, sigma_met=0.0, cuts=None):
+def dilep(sigma_jet=0.0, sigma_met=0.0, cuts=None, sigma_lep=0.0):
     """Dilepton ttH chain D1..D5: opposite-sign leptons, >= 4 jets,
     >= 4 b-tags, two-neutrino solution exists, 100 < m_bb < 150;
     m_bb histogram 50 bins 0-500."""
@@ -61,7 +62,7 @@ def dilep(sigma_jet=0.0, sigma_met=0.0, cuts=None):
                 ("dilep_solvable",), ("higgs_window", 100.0, 150.0)]
     return dict(model="dilep", cuts=list(cuts), mW=80.4, mt=172.5,
                 sigma_t=15.0, sigma_W=10.0, mH=125.0,
-                sigma_jet=sigma_jet, sigma_met=sigma_met, hist=(50, 0.0, 500.0))
+                sigma_jet=sigma_jet, sigma_met=sigma_met, sigma_lep=sigma_lep, hist=(50, 0.0, 500.0))
 
 
 def config1():
@@ -80,9 +81,10 @@ def config3():
 
 
 def tth_sci():
-    """The paper's ttH_sci resolution model on the dilepton chain: 1 % jet
-    energy resolution, MET shifted by N(0, 1 GeV) per component."""
-    return dilep(sigma_jet=0.01, sigma_met=1.0)
+    """The paper's ttH_sci resolution model on the dilepton chain: 1 % on
+    every measured object -- jet and lepton energies scaled by N(1, 0.01),
+    MET shifted by N(0, 1 GeV) per component."""
+    return dilep(sigma_jet=0.01, sigma_met=1.0, sigma_lep=0.01)
 
 
 def with_cuts(an, cuts):

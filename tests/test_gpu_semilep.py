@@ -204,6 +204,24 @@ def test_fetch_timeout_keeps_the_ticket(eng):
         eng.poll(t)  # released by the successful fetch
 
 
+def test_two_contexts_in_one_process(orc):
+    """Two contexts open at once on device 0 (per-device kernel attributes and
+    scratch are per context): each runs the same chunk, interleaved, and both
+    equal the oracle."""
+    from paper_2211_14346_gb300 import Engine, DeviceColumns
+    an = analyses.config2()
+    cols = synth.gen_semilep(3000, 46)
+    o = orc.run(an, cols, seed=8, V=16)
+    with Engine(0) as a, Engine(0) as b:
+        ia, ib = a.define(an), b.define(an)
+        dc = DeviceColumns(cols)
+        for _ in range(2):
+            ga = a.run_device(ia, dc, V=16, seed=8).numpy()
+            gb = b.run_device(ib, dc, V=16, seed=8).numpy()
+            assert_parity(ga, o, what="context a")
+            assert_parity(gb, o, what="context b")
+
+
 def test_malformed_columns_are_rejected(eng):
     from paper_2211_14346_gb300 import DeviceColumns, HostColumnsView, HFError
     from paper_2211_14346_gb300 import _lib
