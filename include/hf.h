@@ -144,7 +144,22 @@ typedef struct {
                             lepton l of a unit is scaled by 1 + sigma_lep z[14 + l] (Sect. 4:
                             every measured object is smeared); with sigma_lep != 0 the lepton
                             pT cut and the W-mass solvability are decided per unit           */
+    uint32_t per_event;  /* HF_PER_EVENT_*: what an event reports from its variations       */
 } hf_analysis_desc;
+
+/* hf_analysis_desc.per_event */
+#define HF_PER_EVENT_MEAN 0u /* reco = mean over the surviving variations; the histogram is
+                                filled once per surviving unit                               */
+#define HF_PER_EVENT_BEST 1u /* best-of-variations (Sect. 4, ttH_sci: of the pseudo-experiments
+                                only the most probable solution is kept): reco = the quantities
+                                of the surviving variation with the smallest fit score -- the
+                                hadronic chi2 of Eq. 1, the full Eq. 1 chi2 with the full fit,
+                                m_ttbar of the chosen solution in the dilepton model -- ties to
+                                the lowest variation; hf_results.best_v receives it; the
+                                histogram is filled once per selected event with that
+                                variation's value.  Device-resident single runs, the
+                                allocation-free run and unbatched submissions; not the plain
+                                form, hf_run_batch or HF_FLAG_BATCHING (HF_EINVAL)            */
 
 /* Variables of the per-cut recording.  A variable is stored at every
  * recorded level; where it is not defined yet at that level it holds its
@@ -199,6 +214,8 @@ typedef struct {
                            points only: hf_fetch_results rejects it)                      */
     uint64_t record_cap; /* records entries; records beyond it are counted, not written */
     uint64_t* n_records; /* 1 (device): records produced (may exceed record_cap)         */
+    uint16_t* best_v;    /* N: with HF_PER_EVENT_BEST, the chosen variation (0xffff without a
+                            surviving one); ignored otherwise                                */
 } hf_results;
 
 /* Asynchronous chunk submission (the serving entry point): a chunk of events
@@ -485,7 +502,7 @@ hf_status hf_fp32_peak(int32_t device, hf_fp32_peak_result* out);
  *     host threads without ordering) race and give wrong results: order them.
  * Errors: HF_EINVAL, HF_ECUDA. */
 #define HF_NOALLOC_MAX_EVENTS 1048576u
-#define HF_NOALLOC_SCRATCH_BYTES 14722304u
+#define HF_NOALLOC_SCRATCH_BYTES 15508736u
 hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const hf_columns* dev_cols, uint64_t n_events,
                                 uint64_t first_event_id, uint64_t seed, uint32_t n_variations,
                                 const hf_results* dev_out, void* stream);

@@ -154,12 +154,15 @@ class DeviceResults:
         self.records = torch.zeros((max(1, self.record_cap), 6), dtype=torch.int32, device=device) \
             if self.record_cap else None
         self.n_records = torch.zeros(1, dtype=torch.int64, device=device) if self.record_cap else None
+        self.best_v = torch.zeros(n_events, dtype=torch.int16, device=device)
 
     def struct(self, fields=None):
         s = _lib.hf_results()
         for f in ("mask", "cutflow", "hist", "n_surv", "reco", "recheck_count"):
             if fields is None or f in fields:
                 setattr(s, f, getattr(self, f).data_ptr())
+        if fields is None or "best_v" in fields:
+            s.best_v = self.best_v.data_ptr()
         if self.records is not None and (fields is None or "records" in fields):
             s.records = self.records.data_ptr()
             s.record_cap = self.record_cap
@@ -170,7 +173,8 @@ class DeviceResults:
         out = dict(mask=self.mask.cpu().numpy(), cutflow=self.cutflow.cpu().numpy().astype(np.uint64),
                    hist=self.hist.cpu().numpy().astype(np.uint64),
                    n_surv=self.n_surv.cpu().numpy().view(np.uint16), reco=self.reco.cpu().numpy(),
-                   recheck_count=int(self.recheck_count.cpu().item()))
+                   recheck_count=int(self.recheck_count.cpu().item()),
+                   best_v=self.best_v.cpu().numpy().view(np.uint16))
         if self.records is not None:
             n = int(self.n_records.cpu().item())
             raw = self.records[:min(n, self.record_cap)].cpu().numpy()
@@ -191,6 +195,7 @@ def analysis_desc(an):
     for k in ("mW", "mt", "sigma_t", "sigma_W", "mH", "sigma_jet", "sigma_met"):
         setattr(d, k, _f32(an[k]))
     d.sigma_lep = _f32(an.get("sigma_lep", 0.0))
+    d.per_event = 1 if an.get("per_event", "mean") == "best" else 0
     nb, lo, hi = an["hist"]
     d.hist_nbins, d.hist_lo, d.hist_hi = int(nb), _f32(lo), _f32(hi)
     rec = an.get("record")
@@ -409,6 +414,8 @@ class Engine:
                 out["reco"] = np.zeros((n_events, N_RECO), np.float32)
             if "recheck_count" in fields:
                 out["recheck_count"] = np.zeros(1, np.uint64)
+            if "best_v" in fields or an.get("per_event") == "best":
+                out["best_v"] = np.zeros(n_events, np.uint16)
         rs = _lib.hf_results()
         for f, a in out.items():
             setattr(rs, f, a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())

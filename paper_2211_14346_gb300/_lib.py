@@ -56,7 +56,8 @@ class hf_analysis_desc(C.Structure):
                 ("mW", C.c_float), ("mt", C.c_float), ("sigma_t", C.c_float), ("sigma_W", C.c_float),
                 ("mH", C.c_float), ("sigma_jet", C.c_float), ("sigma_met", C.c_float),
                 ("hist_nbins", C.c_uint32), ("hist_lo", C.c_float), ("hist_hi", C.c_float),
-                ("record_levels", C.c_uint32), ("record_vars", C.c_uint32 * 4), ("sigma_lep", C.c_float)]
+                ("record_levels", C.c_uint32), ("record_vars", C.c_uint32 * 4), ("sigma_lep", C.c_float),
+                ("per_event", C.c_uint32)]
 
 
 class hf_columns(C.Structure):
@@ -67,7 +68,7 @@ class hf_columns(C.Structure):
 class hf_results(C.Structure):
     _fields_ = [("mask", C.c_void_p), ("cutflow", C.c_void_p), ("hist", C.c_void_p), ("n_surv", C.c_void_p),
                 ("reco", C.c_void_p), ("recheck_count", C.c_void_p), ("records", C.c_void_p),
-                ("record_cap", C.c_uint64), ("n_records", C.c_void_p)]
+                ("record_cap", C.c_uint64), ("n_records", C.c_void_p), ("best_v", C.c_void_p)]
 
 
 class hf_chunk(C.Structure):

@@ -108,7 +108,7 @@ RunLayout layout_for(uint64_t N, uint32_t V)
     L.off_rc_reco = o = align_up(o, 256);
     o += 16 * cap;
     L.off_rc_f = o = align_up(o, 256);
-    o += 4 * cap;
+    o += sizeof(RcRes) * cap;
     L.off_maxf = o = align_up(o, 256);
     o += std::max<uint64_t>(N, 1);
     L.off_rec_pre = o = align_up(o, 256);
@@ -146,7 +146,7 @@ Scratch make_scratch(char* base, const RunLayout& L, const Analysis& A)
     S.pend_cnt = (unsigned*)(base + L.off_pend_cnt);
     S.pend_rng = (uint2*)(base + L.off_pend_rng);
     S.rc_reco = (float4*)(base + L.off_rc_reco);
-    S.rc_f = (int*)(base + L.off_rc_f);
+    S.rc_res = (RcRes*)(base + L.off_rc_f);
     S.rec_pre = (unsigned long long*)(base + L.off_rec_pre);
     S.pend_sum = (float4*)(base + L.off_pend_sum);
     S.pend_comp = (float4*)(base + L.off_pend_comp);
@@ -183,7 +183,7 @@ ColLayout col_layout(uint64_t N, uint64_t J, int L)
 }
 
 struct ResLayout {
-    size_t off_mask, off_nsurv, off_reco, bytes;
+    size_t off_mask, off_nsurv, off_reco, off_bestv, bytes;
 };
 ResLayout res_layout(uint64_t N)
 {
@@ -195,6 +195,8 @@ ResLayout res_layout(uint64_t N)
     o += 2 * N;
     r.off_mask = o = align_up(o, 256);
     o += N;
+    r.off_bestv = o = align_up(o, 256);
+    o += 2 * N;
     r.bytes = align_up(o, 256);
     return r;
 }
@@ -358,6 +360,8 @@ hf_status hf::build_plan(const hf_analysis_desc* d, Plan& P)
     P.sigma_lep = d->sigma_lep;
     P.smear_lep = d->sigma_lep != 0.0f;
     P.dsigma_lep = d->sigma_lep;
+    if (d->per_event > HF_PER_EVENT_BEST) return fail(HF_EINVAL, "per_event must be HF_PER_EVENT_MEAN or _BEST");
+    P.best = d->per_event == HF_PER_EVENT_BEST;
     P.nbins = (int)d->hist_nbins;
     P.lo = d->hist_lo;
     P.hi = d->hist_hi;
@@ -432,6 +436,7 @@ hf_status ensure_arena(hf_ctx* ctx, size_t bytes)
 hf_status records_out(const Analysis& A, const hf_results& r, Out& O)
 {
     if (!r.records || !A.plan.rec_levels) return HF_OK;
+    if (A.plan.best) return fail(HF_EINVAL, "per-cut records are not kept with best-of-variations");
     if (!r.n_records) return fail(HF_EINVAL, "records given without n_records");
     if ((uintptr_t)r.records & 3) return fail(HF_EINVAL, "records must be 4-byte aligned");
     for (int i = 0; i < 4; ++i)
@@ -465,6 +470,7 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
     if (N > 0xFFFFFFFFull) return fail(HF_EINVAL, "at most 2^32 - 1 events per call");
     if (N == 0) return HF_OK;
     bool use_plain = plain || (ctx->flags & HF_FLAG_PLAIN);
+    if (use_plain && A.plan.best) return fail(HF_EINVAL, "best-of-variations does not run in the plain form");
     if (use_plain) S.exec2 = nullptr;
     cudaEvent_t* evp = nullptr;
     std::array<cudaEvent_t, 4> ev{};
@@ -534,6 +540,7 @@ hf_status run_device_impl(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* d
         O.cutflow = (unsigned long long*)dev_out->cutflow;
         O.hist = (unsigned long long*)dev_out->hist;
         O.rc_total = (unsigned long long*)dev_out->recheck_count;
+        if (A->plan.best) O.best_v = dev_out->best_v;
         if (dev_out->reco && ((uintptr_t)dev_out->reco & 15)) return fail(HF_EINVAL, "reco must be 16-byte aligned");
         if (hf_status rs = records_out(*A, *dev_out, O)) return rs;
     }
@@ -734,7 +741,10 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
     if (N > 0 && hc->jet_off[0] != 0) return fail(HF_EINVAL, "jet_off[0] must be 0");
     if (N > 0 && hc->jet_off[N] != hc->n_jets_total) return fail(HF_EINVAL, "jet_off[N] != n_jets_total");
     if (ctx->tickets.size() >= ctx->max_inflight) return fail(HF_EBUSY, "too many in-flight tickets");
-    if (ctx->flags & HF_FLAG_BATCHING) return submit_batched(ctx, analysis_id, *A, hc, N, first_event_id, seed, V, ticket);
+    if (ctx->flags & HF_FLAG_BATCHING) {
+        if (A->plan.best) return fail(HF_EINVAL, "best-of-variations analyses do not run batched");
+        return submit_batched(ctx, analysis_id, *A, hc, N, first_event_id, seed, V, ticket);
+    }
     const uint64_t J = hc->n_jets_total;
     ColLayout CL = col_layout(N, J, L);
     RunLayout RL = layout_for(N, V);
@@ -782,6 +792,7 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
     O.mask = (uint8_t*)(dres + RR.off_mask);
     O.n_surv = (uint16_t*)(dres + RR.off_nsurv);
     O.reco = (float4*)(dres + RR.off_reco);
+    if (A->plan.best) O.best_v = (uint16_t*)(dres + RR.off_bestv);
     hf_status s = enqueue_run(ctx, *A, C, N, V, O, dscr, RL, seed, first_event_id, false, ctx->s_comp);
     HF_CUDA(cudaEventCreateWithFlags(&T.done, cudaEventDisableTiming));
     HF_CUDA(cudaEventRecord(T.done, ctx->s_comp));
@@ -885,6 +896,8 @@ hf_status hf_fetch_results(hf_ctx* ctx, uint64_t ticket, hf_results* out, uint32
             e = cudaMemcpyAsync(out->n_surv, d_res + T.R.off_nsurv, 2 * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->reco && N)
             e = cudaMemcpyAsync(out->reco, d_res + T.R.off_reco, 16 * N, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out->best_v && N && A->plan.best && !T.batched)
+            e = cudaMemcpyAsync(out->best_v, d_res + T.R.off_bestv, 2 * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->cutflow)
             e = cudaMemcpyAsync(out->cutflow, d_cf, 8 * (nc + 1), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out->hist)
@@ -1056,6 +1069,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
             if (!A) return fail(HF_ENOTFOUND, "a chunk names an unknown analysis id");
             const int cls = A->plan.model == MODEL_DILEP ? 2 : (A->plan.has_full ? 1 : 0);
             if (cls != pass) continue;
+            if (A->plan.best) return fail(HF_EINVAL, "best-of-variations analyses do not run batched");
             if (pass == 0) ++n_semi0;
             if (k.n_variations < 1 || k.n_variations > HF_MAX_VARIATIONS)
                 return fail(HF_EINVAL, "a chunk's n_variations is outside 1..4096");
@@ -1118,7 +1132,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         if (P.model == MODEL_DILEP) {
             b.ept = (uint32_t)dl_ev_per_tile(b.V, ctx->tune[2][vclass(b.V)]);
             BL.dilep = true;
-            BL.smem_dilep = std::max(BL.smem_dilep, smem_class(dl_smem_bytes((int)b.ept, (int)(b.ept * b.V))));
+            BL.smem_dilep = std::max(BL.smem_dilep, smem_class(dl_smem_bytes((int)b.ept, (int)(b.ept * b.V), false)));
             units_dl += units;
         } else {
             b.ept = (uint32_t)ev_per_tile_for(b.V, ctx->tune[1][vclass(b.V)]);
@@ -1176,7 +1190,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
     L.off_rc_reco = o = align_up(o, 256);
     o += 16 * cap;
     L.off_rc_f = o = align_up(o, 256);
-    o += 4 * cap;
+    o += sizeof(RcRes) * cap;
     L.off_maxf = o = align_up(o, 256);
     o += std::max<uint64_t>(ev_total, 1);
     L.off_rec_pre = o = align_up(o, 256);
@@ -1231,7 +1245,7 @@ hf_status batch_enqueue(hf_ctx* ctx, const hf_chunk* chunks, uint32_t n_chunks, 
         S.pend_cnt = (unsigned*)(dbase + L.off_pend_cnt);
         S.pend_rng = (uint2*)(dbase + L.off_pend_rng);
         S.rc_reco = (float4*)(dbase + L.off_rc_reco);
-        S.rc_f = (int*)(dbase + L.off_rc_f);
+        S.rc_res = (RcRes*)(dbase + L.off_rc_f);
         S.pend_sum = (float4*)(dbase + L.off_pend_sum);
         S.pend_comp = (float4*)(dbase + L.off_pend_comp);
         S.stats = nullptr;

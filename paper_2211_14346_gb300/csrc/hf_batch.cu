@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(BLOCK) k_brecheck(const BatchDev* __restrict__
         atomicAdd(ch.O.rc_total, 1ull);
         if (f == P.n_cuts) atomicAdd(&ch.O.hist[bin], 1ull);
         S.rc_reco[i] = reco;
-        S.rc_f[i] = f;
+        S.rc_res[i] = RcRes{f, bin, 0.0};
     }
 }
 

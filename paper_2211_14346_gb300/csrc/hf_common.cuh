@@ -16,6 +16,7 @@ __device__ __forceinline__ void write_zero_event(const Out& O, uint32_t e)
     if (O.n_surv) O.n_surv[e] = 0;
     if (O.reco) O.reco[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (O.maxf) O.maxf[e] = 0;
+    if (O.best_v) O.best_v[e] = 0xffffu;
 }
 
 // ------------------------------------------------------------------ per-cut records
@@ -282,7 +283,7 @@ static __device__ __noinline__ double hadtop_screened_d(const Plan& P, LazyUnitD
 
 // Dilepton unit with the definition's FP64 arithmetic (user order).
 static __device__ __noinline__ int dilep_unit_fp64(const Plan& P, const Cols& C, uint32_t e, LazyUnitD& U,
-                                                   unsigned s1bits, float4* reco, int* bin)
+                                                   unsigned s1bits, float4* reco, int* bin, double* score)
 {
     const float2 mf = C.met[e];
     double l1[4], l2[4];
@@ -328,19 +329,23 @@ static __device__ __noinline__ int dilep_unit_fp64(const Plan& P, const Cols& C,
         }
         *bin = hist_bin_d(P, r.m_bb);
         *reco = make_float4((float)r.m_bb, (float)r.m_t1, (float)r.m_t2, (float)r.m_tt);
+        if (score) *score = r.m_tt;
     }
     return f;
 }
 
 // One unit with the definition's FP64 decisions (user order; stage-1
 // results are already exact and are taken from s1bits).  Returns the number
-// of leading cuts passed; reco and bin are set when all pass.
-static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id, uint64_t seed,
-                         uint32_t v, unsigned s1bits, float4* reco, int* bin)
+// of leading cuts passed; reco, bin and (when given) the fit score -- the
+// chi2 of the analysis's fit, or m_ttbar of the dilepton solution -- are set
+// when all pass.  Called through unit_fp64 / unit_fp64_scored below.
+__device__ __forceinline__ int unit_fp64_body(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id,
+                                              uint64_t seed, uint32_t v, unsigned s1bits, float4* reco, int* bin,
+                                              double* score)
 {
     LazyUnitD U;
     U.init(P, C, e, event_id, seed, v);
-    if (P.model == MODEL_DILEP) return dilep_unit_fp64(P, C, e, U, s1bits, reco, bin);
+    if (P.model == MODEL_DILEP) return dilep_unit_fp64(P, C, e, U, s1bits, reco, bin, score);
     const float2 mf = C.met[e];
     bool top_done = false, full_done = false;
     double chi2 = 0.0, mtop = 0.0, mw = 0.0;
@@ -388,6 +393,7 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         const double met = sqrt(U.metx * U.metx + U.mety * U.mety);
         *bin = hist_bin_d(P, ff.mtop_had);
         *reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, (float)met);
+        if (score) *score = ff.chi2;
     } else if (f == P.n_cuts) {
         if (!top_done) chi2 = hadtop_screened_d(P, U, &mtop, &mw);
         U.met(mf);
@@ -396,8 +402,25 @@ static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint3
         double met = sqrt(U.metx * U.metx + U.mety * U.mety);
         *bin = hist_bin_d(P, mtop);
         *reco = make_float4((float)mtop, (float)mw, (float)pz, (float)met);
+        if (score) *score = chi2;
     }
     return f;
+}
+
+// Out of line, without and with the score: the stage-2 kernels call the
+// former on their rarely taken paths, and an extra argument there cost their
+// register allocation spills in the unit loop (measured).
+static __device__ __noinline__ int unit_fp64(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id, uint64_t seed,
+                                             uint32_t v, unsigned s1bits, float4* reco, int* bin)
+{
+    return unit_fp64_body(P, C, e, event_id, seed, v, s1bits, reco, bin, nullptr);
+}
+
+static __device__ __noinline__ int unit_fp64_scored(const Plan& P, const Cols& C, uint32_t e, uint64_t event_id,
+                                                    uint64_t seed, uint32_t v, unsigned s1bits, float4* reco, int* bin,
+                                                    double* score)
+{
+    return unit_fp64_body(P, C, e, event_id, seed, v, s1bits, reco, bin, score);
 }
 
 // The records of one block of events (thread = event e, valid if `has`),
@@ -612,7 +635,7 @@ __device__ __forceinline__ void finish_pending(const Scratch& S, int n_cuts, uns
     cnt = 0;
     maxf = -1;
     for (unsigned i = lane; i < rg.y; i += 32) {
-        const int f = S.rc_f[rg.x + i];
+        const int f = S.rc_res[rg.x + i].f;
         maxf = max(maxf, f);
         if (f == n_cuts) {
             ++cnt;
@@ -635,6 +658,7 @@ __device__ __forceinline__ void finish_pending(const Scratch& S, int n_cuts, uns
 // Adds a warp's units to the block's cut flow, histogram and scheduler
 // statistics with one shared-memory atomic per distinct value (lanes with the
 // same first-failure index or bin are combined by __match_any_sync).
+template <bool BEST = false>
 __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsigned long long* fc, unsigned* hist,
                                            CutStats* st)
 {
@@ -642,7 +666,7 @@ __device__ __forceinline__ void warp_tally(const Plan& P, const UnitOut& r, unsi
     const unsigned lane = threadIdx.x & 31u;
     const unsigned g = __match_any_sync(am, r.f);
     if (r.f >= 0 && lane == (unsigned)(__ffs(g) - 1)) atomicAdd(&fc[r.f], (unsigned long long)__popc(g));
-    const int hb = r.f == P.n_cuts ? r.bin : -1;
+    const int hb = r.f == P.n_cuts && !BEST ? r.bin : -1;  // best-of: filled per event
     const unsigned gh = __match_any_sync(am, hb);
     if (hb >= 0 && lane == (unsigned)(__ffs(gh) - 1)) atomicAdd(&hist[hb], (unsigned)__popc(gh));
     const bool leader = lane == (unsigned)(__ffs(am) - 1);
@@ -803,18 +827,267 @@ __device__ inline void reduce_events_grp(const Plan& P, const Cols& C, const Out
     }
 }
 
-// Per-event reduction of a tile's units: compensated sums of the surviving
-// units' reconstructed quantities; events without flagged units are written,
+// ------------------------------------------------------------------ best-of-variations
+// Per-event best-of-variations (Sect. 4, ttH_sci): of an event's surviving
+// variations the one with the smallest fit score (the triplet chi2 of Eq. 1,
+// the full Eq. 1 chi2 with the full fit, m_ttbar of the dilepton solution),
+// ties to the lowest variation.  Recheck entries that carry RC_SCORE_ONLY in
+// vbits are certain survivors listed only for their FP64 score: the cut flow
+// already holds them.
+constexpr uint32_t RC_SCORE_ONLY = 0x8000u;
+
+// Half-width of an interval certain to hold the definition's FP64 score of an
+// unflagged survivor whose FP32 score is s: the chi2 band of the triplet fit;
+// the full fit and the dilepton m_ttbar are FP64 values rounded to FP32
+// (2^-24 relative) whose solution choice already keeps a 1e-8 relative margin.
+__device__ __forceinline__ float best_band(const Plan& P, float s)
+{
+    if (P.model == MODEL_SEMILEP && !P.has_full) return chi2_band(P, s);
+    return P.safety * (1.2e-7f * fabsf(s)) + 1.0e-30f;
+}
+
+__device__ __forceinline__ void write_event_best(const Out& O, uint32_t e, unsigned cnt, unsigned vb, float4 reco)
+{
+    if (O.mask) O.mask[e] = cnt > 0;
+    if (O.n_surv) O.n_surv[e] = (uint16_t)cnt;
+    if (O.reco) O.reco[e] = cnt ? reco : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (O.best_v) O.best_v[e] = cnt ? (uint16_t)vb : (uint16_t)0xffffu;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_sum(unsigned x)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, G);
+    return x;
+}
+
+// Lexicographic minimum of (k, v) over a lane group; every lane of the group
+// receives it.
+template <int G, class T>
+__device__ __forceinline__ void group_argmin(T& k, unsigned& v)
+{
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) {
+        const T k2 = __shfl_xor_sync(0xffffffffu, k, o, G);
+        const unsigned v2 = __shfl_xor_sync(0xffffffffu, v, o, G);
+        if (k2 < k || (k2 == k && v2 < v)) {
+            k = k2;
+            v = v2;
+        }
+    }
+}
+
+// Per-event best-of reduction by groups of G lanes (as reduce_events_grp).
+// Among the certain survivors, vmin has the smallest upper score bound umin;
+// the event is decided here when no unit is flagged and every other
+// survivor's lower bound lies above umin.  Otherwise the flagged units and
+// the survivors whose interval reaches umin (vmin among them) are listed:
+// the best of the event is one of them, chosen in FP64 at completion.
+template <int G>
+__device__ inline void reduce_events_best(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
+                                          uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
+                                          const uint32_t* bits, const int* uf, const float4* ureco,
+                                          const float2* usc, unsigned long long* fc, unsigned* hist, int rank,
+                                          int size)
+{
+    const unsigned lane = (unsigned)rank & 31u;
+    const unsigned gl = lane & (unsigned)(G - 1);
+    const unsigned g0 = lane - gl;
+    const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    const unsigned below = (1u << gl) - 1u;
+    constexpr int GPW = 32 / G;
+    const int gid = (rank >> 5) * GPW + (int)(lane / G);
+    const int ngroups = (size >> 5) * GPW;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int ev0 = 0; ev0 < ne; ev0 += ngroups) {
+        const int ev = ev0 + gid;
+        const bool valid = ev < ne;
+        const uint32_t e = valid ? evid[ev] : 0u;
+        const int u0 = ev * (int)V;
+        unsigned cnt = 0, nflag = 0;
+        int mf = 0;
+        float umin = CUDART_INF_F;
+        unsigned vmin = 0xffffffffu;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            const bool in = valid && v < V;
+            const int f = in ? uf[u0 + (int)v] : -1;
+            nflag += __popc((__ballot_sync(0xffffffffu, in && f < 0) >> g0) & gbits);
+            if (in && f == P.n_cuts) {
+                ++cnt;
+                const float sc = usc[u0 + (int)v].x;
+                const float up = __fadd_ru(sc, best_band(P, sc));
+                if (up < umin) {
+                    umin = up;
+                    vmin = v;
+                }
+            }
+            mf = max(mf, f);
+        }
+        cnt = group_sum<G>(cnt);
+        group_argmin<G>(umin, vmin);
+        // a survivor is close when its interval reaches umin
+        auto close = [&](uint32_t v) {
+            const float sc = usc[u0 + (int)v].x;
+            return v == vmin || __fsub_rd(sc, best_band(P, sc)) <= umin;
+        };
+        unsigned nclose = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            if (valid && v < V && v != vmin && uf[u0 + (int)v] == P.n_cuts && close(v)) ++nclose;
+        }
+        nclose = group_sum<G>(nclose);
+        if (O.maxf) {
+            mf = group_max<G>(mf);
+            if (valid && gl == 0) O.maxf[e] = (uint8_t)max(mf, 0);
+        }
+        const bool certain = nflag == 0 && nclose == 0;
+        if (valid && certain && gl == 0) {
+            float4 r = zero;
+            if (cnt) {
+                const int u = u0 + (int)vmin;
+                r = ureco[u];
+                atomicAdd(&hist[__float_as_int(usc[u].y)], 1u);
+            }
+            write_event_best(O, e, cnt, vmin, r);
+        }
+        const bool pend = valid && !certain;
+        if (!__any_sync(0xffffffffu, pend)) continue;
+        const unsigned nlist = nflag + (cnt ? nclose + 1u : 0u);
+        unsigned base = 0, slot = 0;
+        int ok = 0;
+        if (pend && gl == 0) ok = reserve_pending(S, nlist, cnt, zero, zero, base, slot);
+        ok = __shfl_sync(0xffffffffu, ok, g0);
+        base = __shfl_sync(0xffffffffu, base, g0);
+        slot = __shfl_sync(0xffffffffu, slot, g0);
+        const bool listed = pend && ok;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            const int f = listed && v < V ? uf[u0 + (int)v] : -2;
+            const bool fl = f == -1;
+            const bool so = f == P.n_cuts && close(v);
+            const unsigned m = (__ballot_sync(0xffffffffu, fl || so) >> g0) & gbits;
+            if (fl || so) S.rc[base + __popc(m & below)] = rc_entry(S, e, v | (so ? RC_SCORE_ONLY : 0u), bits[ev], slot);
+            base += __popc(m);
+        }
+        // list full: the group's lanes evaluate the listed units in FP64
+        const bool inl = pend && !ok;
+        if (!__any_sync(0xffffffffu, inl)) continue;
+        double bs = CUDART_INF;
+        unsigned bv = 0xffffffffu, n2 = 0, nrc = 0;
+        float4 br = zero;
+        int bb = 0, mf2 = 0;
+        for (uint32_t v0 = 0; v0 < V; v0 += G) {
+            const uint32_t v = v0 + gl;
+            const int f = inl && v < V ? uf[u0 + (int)v] : -2;
+            const bool fl = f == -1;
+            if (!(fl || (f == P.n_cuts && close(v)))) continue;
+            float4 reco;
+            int bin = 0;
+            double sc = CUDART_INF;
+            const int f2 = unit_fp64_scored(P, C, e, first_id + e, seed, v, bits[ev], &reco, &bin, &sc);
+            ++nrc;
+            if (fl) {
+                atomicAdd(&fc[f2], 1ull);
+                mf2 = max(mf2, f2);
+                if (f2 == P.n_cuts) ++n2;
+            }
+            if (f2 == P.n_cuts && sc < bs) {  // a lane's variations increase: ties keep the lower
+                bs = sc;
+                bv = v;
+                br = reco;
+                bb = bin;
+            }
+        }
+        __syncwarp();
+        unsigned kv = bv;
+        group_argmin<G>(bs, kv);
+        const int wl = (int)(g0 + (kv & (unsigned)(G - 1)));  // the lane that evaluated the winner
+        br.x = __shfl_sync(0xffffffffu, br.x, wl);
+        br.y = __shfl_sync(0xffffffffu, br.y, wl);
+        br.z = __shfl_sync(0xffffffffu, br.z, wl);
+        br.w = __shfl_sync(0xffffffffu, br.w, wl);
+        bb = __shfl_sync(0xffffffffu, bb, wl);
+        n2 = group_sum<G>(n2);
+        nrc = group_sum<G>(nrc);
+        mf2 = group_max<G>(mf2);
+        if (inl && gl == 0) {
+            if (O.maxf) O.maxf[e] = (uint8_t)max((int)O.maxf[e], mf2);
+            atomicAdd(O.rc_total, (unsigned long long)nrc);
+            if (kv != 0xffffffffu) atomicAdd(&hist[bb], 1u);
+            write_event_best(O, e, cnt + n2, kv, br);
+        }
+    }
+}
+
+// Completion of best-of pending slot s by one warp: the FP64 argmin over the
+// listed survivors; hist is the run's histogram.  Lane 0 writes the event.
+__device__ __forceinline__ void finish_pending_best(const Out& O, const Scratch& S, int n_cuts, unsigned s,
+                                                    unsigned long long* hist, int& maxf, RcEntry& first)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const uint2 rg = S.pend_rng[s];
+    unsigned cnt = 0, bv = 0xffffffffu, bi = 0;
+    double bs = CUDART_INF;
+    maxf = -1;
+    for (unsigned i = lane; i < rg.y; i += 32) {
+        const RcRes q = S.rc_res[rg.x + i];
+        const uint32_t vb = S.rc[rg.x + i].vbits;
+        const unsigned v = vb & 0x7fffu;
+        if (!(vb & RC_SCORE_ONLY)) {
+            maxf = max(maxf, q.f);
+            if (q.f == n_cuts) ++cnt;
+        }
+        if (q.f == n_cuts && (q.score < bs || (q.score == bs && v < bv))) {
+            bs = q.score;
+            bv = v;
+            bi = rg.x + i;
+        }
+    }
+    cnt = group_sum<32>(cnt);
+    maxf = __reduce_max_sync(0xffffffffu, maxf);
+    unsigned key = bv;
+    group_argmin<32>(bs, key);
+    // the winner's entry index: the lane that held it publishes it
+    const unsigned holder = __ballot_sync(0xffffffffu, bv == key && key != 0xffffffffu);
+    const unsigned wi = holder ? __shfl_sync(0xffffffffu, bi, __ffs(holder) - 1) : 0u;
+    if (lane == 0) {
+        first = S.rc[rg.x];
+        cnt += S.pend_cnt[s];
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (key != 0xffffffffu) {
+            r = S.rc_reco[wi];
+            atomicAdd(&hist[S.rc_res[wi].bin], 1ull);
+        }
+        write_event_best(O, first.event, cnt, key, r);
+    }
+}
+
+// Per-event reduction of a tile's units (BEST: best-of-variations, above;
+// the mean otherwise): compensated sums of the surviving units' reconstructed
+// quantities; events without flagged units are written,
 // the others get a pending slot and their flagged units go to the recheck
 // list.  Fewer than 5 variations: one thread per event, in variation order;
 // otherwise a group of 8, 16 or 32 lanes per event (reduce_events_grp), so
 // that no thread walks many variations while the others wait.  rank and size
 // describe the calling group (size a multiple of 32, every thread calls).
+template <bool BEST>
 __device__ inline void reduce_tile_events(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                                           uint64_t seed, uint64_t first_id, int ne, const uint32_t* evid,
                                           const uint32_t* bits, const int* uf, const float4* ureco,
-                                          unsigned long long* fc, unsigned* hist, int rank, int size)
+                                          const float2* usc, unsigned long long* fc, unsigned* hist, int rank,
+                                          int size)
 {
+    if constexpr (BEST) {
+        if (V > 16)
+            reduce_events_best<32>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, usc, fc, hist, rank, size);
+        else if (V > 8)
+            reduce_events_best<16>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, usc, fc, hist, rank, size);
+        else
+            reduce_events_best<8>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, usc, fc, hist, rank, size);
+        return;
+    }
     if (V > 16) {
         reduce_events_grp<32>(P, C, O, S, V, seed, first_id, ne, evid, bits, uf, ureco, fc, hist, rank, size);
         return;
@@ -874,22 +1147,25 @@ struct TileSmem {
     uint32_t* evid; // [ev]
     uint32_t* bits; // [ev]
     float4* ureco;  // [unit]
+    float2* usc;    // [unit] fit score and (bits of) bin, best-of-variations only
     int* uf;        // [unit] f or -1
     char* top;      // the chi2 step's region (16-byte aligned, after the above)
 };
 
-__host__ __device__ inline size_t tile_smem_bytes(int ev, int units, int gst)
+// best: room for the units' scores (best-of-variations runs only).
+__host__ __device__ inline size_t tile_smem_bytes(int ev, int units, int gst, bool best)
 {
-    return (size_t)ev * ((size_t)gst * 4 + 16 + 8 + 4 + 4) + (size_t)units * (16 + 4) + 64;
+    return (size_t)ev * ((size_t)gst * 4 + 16 + 8 + 4 + 4) + (size_t)units * (16 + (best ? 8 : 0) + 4) + 64;
 }
 
-__device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap, int gst)
+__device__ inline TileSmem carve(char* p, int ev_cap, int unit_cap, int gst, bool best)
 {
     TileSmem t;
-    t.top = p + ((tile_smem_bytes(ev_cap, unit_cap, gst) + 15) & ~(size_t)15);
+    t.top = p + ((tile_smem_bytes(ev_cap, unit_cap, gst, best) + 15) & ~(size_t)15);
     t.ureco = (float4*)p; p += (size_t)unit_cap * 16;
     t.lep = (float4*)p; p += (size_t)ev_cap * 16;
     t.met = (float2*)p; p += (size_t)ev_cap * 8;
+    t.usc = (float2*)p; p += best ? (size_t)unit_cap * 8 : 0;
     t.G = (float*)p; p += (size_t)ev_cap * gst * 4;
     t.evid = (uint32_t*)p; p += (size_t)ev_cap * 4;
     t.bits = (uint32_t*)p; p += (size_t)ev_cap * 4;
@@ -931,9 +1207,9 @@ __device__ inline TopSmem carve_top(char* p, int n)
 }
 
 // Dynamic shared memory of a semileptonic stage-2 tile (multiplicity n).
-__host__ __device__ inline size_t semi_smem_bytes(int n, bool full, int ev, int units)
+__host__ __device__ inline size_t semi_smem_bytes(int n, bool full, int ev, int units, bool best)
 {
-    const size_t t = (tile_smem_bytes(ev, units, gram_stride(n)) + 15) & ~(size_t)15;
+    const size_t t = (tile_smem_bytes(ev, units, gram_stride(n), best) + 15) & ~(size_t)15;
     return full ? t : t + top_smem_bytes(n);
 }
 

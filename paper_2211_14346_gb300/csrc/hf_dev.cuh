@@ -58,6 +58,7 @@ struct Plan {
     float mW2half, mW2half_lo;  // mW*mW/2 (exact in FP64) as a float-float pair
     float sigma_jet, sigma_met, sigma_lep;
     int smear_jets, smear_met, smear_lep;
+    int best;          // per-event best-of-variations (HF_PER_EVENT_BEST) instead of the mean
     int nbins;
     float lo, hi, w;   // histogram
     // FP32 error model (relative / absolute bounds vs the FP64 definition)
@@ -102,6 +103,7 @@ struct Out {
     unsigned long long rec_cap;
     unsigned long long* n_rec;    // records produced
     uint8_t* maxf;                // [N] scratch of a recording run: most cuts passed by a variation
+    uint16_t* best_v;             // [N] best-of-variations: the chosen variation (or null)
 };
 
 // Recheck list entry: one unit whose FP32 evaluation came within an error
@@ -111,6 +113,13 @@ struct RcEntry {
     uint32_t vbits;   // variation (low 16 bits) | stage-1 pass bits of the event << 16
     uint32_t slot;    // pending-event slot
     uint32_t chunk;   // chunk of a batched run (0 for a single chunk)
+};
+
+// FP64 result of one recheck entry.
+struct RcRes {
+    int f;         // cuts passed in user order
+    int bin;       // histogram bin when f == n_cuts
+    double score;  // the unit's fit score (best-of-variations; the definition's FP64 value)
 };
 
 struct Scratch {
@@ -125,7 +134,7 @@ struct Scratch {
     RcEntry* rc;          // [rc_cap] flagged units; those of one event are contiguous, in variation order
     unsigned rc_cap;
     float4* rc_reco;      // [rc_cap] FP64 result of entry i: reconstructed quantities
-    int* rc_f;            // [rc_cap] FP64 result of entry i: cuts passed in user order
+    RcRes* rc_res;        // [rc_cap] FP64 result of entry i: cuts passed, bin, score
     unsigned* pend_cnt;   // [rc_cap] surviving unflagged units of pending event s
     unsigned long long* rec_pre; // [stage-1 blocks + 1] records per block, then their exclusive prefix
     uint2* pend_rng;      // [rc_cap] (first entry, number of entries) of pending event s

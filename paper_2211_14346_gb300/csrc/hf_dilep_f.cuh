@@ -375,6 +375,7 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
     out.f = -1;
     out.reco = make_float4(0.f, 0.f, 0.f, 0.f);
     out.bin = 0;
+    out.score = 0.0f;
     out.evald = out.passd = out.cyc_top = out.cyc_met = out.cands = 0;
     const unsigned bm = btag & ((1u << n) - 1u);
     const bool smear = P.smear_jets || P.smear_met || P.smear_lep;
@@ -493,6 +494,7 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
         if (fabs(rel - rint(rel)) * wd <= 1.0e-9 * (fabs(reco.mbb) + 1.0)) return out;  // at an edge
         out.bin = bin;
         out.reco = make_float4((float)reco.mbb, (float)reco.mt1, (float)reco.mt2, (float)reco.mtt);
+        out.score = (float)reco.mtt;
     }
     out.f = f;
     return out;

@@ -107,12 +107,17 @@ __global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, c
         RcEntry r = S.rc[i];
         float4 reco;
         int bin = 0;
-        int f = unit_fp64(P, C, r.event, first_id + r.event, seed, r.vbits & 0xffffu, r.vbits >> 16, &reco, &bin);
+        double score = 0.0;
+        const uint32_t v = r.vbits & 0x7fffu;
+        int f = P.best ? unit_fp64_scored(P, C, r.event, first_id + r.event, seed, v, r.vbits >> 16, &reco, &bin, &score)
+                       : unit_fp64(P, C, r.event, first_id + r.event, seed, v, r.vbits >> 16, &reco, &bin);
         ++mine;
-        atomicAdd(&s_fc[f], 1ull);
-        if (f == P.n_cuts) atomicAdd(&s_hist[bin], 1u);
+        // best-of: score-only entries are in the cut flow already, the
+        // histogram is filled per event at completion
+        if (!(r.vbits & RC_SCORE_ONLY)) atomicAdd(&s_fc[f], 1ull);
+        if (f == P.n_cuts && !P.best) atomicAdd(&s_hist[bin], 1u);
         S.rc_reco[i] = reco;
-        S.rc_f[i] = f;
+        S.rc_res[i] = RcRes{f, bin, score};
     }
     if (mine) atomicAdd(O.rc_total, mine);
     __syncthreads();
@@ -156,6 +161,12 @@ __global__ void __launch_bounds__(BLOCK) k_finish(const Plan P, const Cols C, co
         float4 sum, comp;
         int maxf;
         RcEntry first;
+        if (P.best) {
+            finish_pending_best(O, S, P.n_cuts, s, O.hist, maxf, first);
+            if ((threadIdx.x & 31u) == 0 && O.maxf)
+                O.maxf[first.event] = (uint8_t)max((int)O.maxf[first.event], maxf);
+            continue;
+        }
         finish_pending(S, P.n_cuts, s, cnt, sum, comp, maxf, first);
         if ((threadIdx.x & 31u) == 0) {
             write_event(O, first.event, cnt, sum, comp);
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(BLOCK) k_finish(const Plan P, const Cols C, co
 // ------------------------------------------------------------------ host launchers
 // The larger of the two layouts (with and without the chi2 step), so that a
 // batch's kernels of either kind fit.
-size_t semi_tile_bytes(int n, int ept, int units) { return semi_smem_bytes(n, false, ept, units); }
+size_t semi_tile_bytes(int n, int ept, int units) { return semi_smem_bytes(n, false, ept, units, false); }
 
 cudaError_t ensure_smem_attr(const void* fn)
 {

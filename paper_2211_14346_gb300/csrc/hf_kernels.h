@@ -73,7 +73,7 @@ cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream
 cudaError_t launch_batch(const BatchDev* B, const BatchLaunch& L, cudaStream_t st, const SideStreams* side);
 // Shared memory of one stage-2 tile (semileptonic multiplicity n / dilepton).
 size_t semi_tile_bytes(int n, int ept, int units);
-size_t dl_smem_bytes(int ev, int units);
+size_t dl_smem_bytes(int ev, int units, bool best);
 // Events per tile of the dilepton stage-2 kernel (upt: units per tile, 0 = default).
 int dl_ev_per_tile(uint32_t V, int upt = 0);
 

@@ -34,8 +34,8 @@ constexpr size_t NA_PEND_RNG = NA_PEND_CNT + 4 * (size_t)NA_RC_CAP;   // uint2[N
 constexpr size_t NA_PEND_SUM = NA_PEND_RNG + 8 * (size_t)NA_RC_CAP;   // float4[NA_RC_CAP]
 constexpr size_t NA_PEND_COMP = NA_PEND_SUM + 16 * (size_t)NA_RC_CAP;
 constexpr size_t NA_RC_RECO = NA_PEND_COMP + 16 * (size_t)NA_RC_CAP;  // float4[NA_RC_CAP]
-constexpr size_t NA_RC_F = NA_RC_RECO + 16 * (size_t)NA_RC_CAP;       // int[NA_RC_CAP]
-constexpr size_t NA_MAXF = NA_RC_F + 4 * (size_t)NA_RC_CAP;           // u8[NA_MAX_EVENTS]
+constexpr size_t NA_RC_F = NA_RC_RECO + 16 * (size_t)NA_RC_CAP;       // RcRes[NA_RC_CAP]
+constexpr size_t NA_MAXF = NA_RC_F + sizeof(RcRes) * (size_t)NA_RC_CAP; // u8[NA_MAX_EVENTS]
 constexpr size_t NA_REC_PRE = NA_MAXF + NA_MAX_EVENTS;                 // u64[NA_MAX_EVENTS/256 + 1]
 constexpr size_t NA_CUTFLOW = NA_REC_PRE + 8 * (NA_MAX_EVENTS / 256) + 256;  // u64[MAX_CUTS+1]
 constexpr size_t NA_HIST = NA_CUTFLOW + 256;                          // u64[MAX_BINS+2]
@@ -130,7 +130,7 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
     S.pend_cnt = (unsigned*)(base + NA_PEND_CNT);
     S.pend_rng = (uint2*)(base + NA_PEND_RNG);
     S.rc_reco = (float4*)(base + NA_RC_RECO);
-    S.rc_f = (int*)(base + NA_RC_F);
+    S.rc_res = (RcRes*)(base + NA_RC_F);
     S.rec_pre = (unsigned long long*)(base + NA_REC_PRE);
     S.pend_sum = (float4*)(base + NA_PEND_SUM);
     S.pend_comp = (float4*)(base + NA_PEND_COMP);
@@ -148,7 +148,9 @@ extern "C" hf_status hf_run_device_noalloc(const hf_analysis_desc* desc, const h
         O.cutflow = (unsigned long long*)dev_out->cutflow;
         O.hist = (unsigned long long*)dev_out->hist;
         O.rc_total = (unsigned long long*)dev_out->recheck_count;
+        if (P.best) O.best_v = dev_out->best_v;
         if (dev_out->records && P.rec_levels) {
+            if (P.best) return set_error(HF_EINVAL, "per-cut records are not kept with best-of-variations");
             if (!dev_out->n_records || ((uintptr_t)dev_out->records & 3))
                 return set_error(HF_EINVAL, "records need n_records and 4-byte alignment");
             for (int i = 0; i < 4; ++i)

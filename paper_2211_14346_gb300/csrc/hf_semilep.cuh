@@ -34,6 +34,7 @@ struct UnitOut {
     int f;             // cuts passed in user order (n_cuts = survives); -1 = recheck
     float4 reco;       // (m_top, m_W, pz_nu, |MET|) when f == n_cuts
     int bin;           // histogram bin when f == n_cuts
+    float score;       // fit score when f == n_cuts (FP32; best-of-variations)
     unsigned evald;    // stage-2 cuts evaluated (bit = user index)
     unsigned passd;    // stage-2 cuts passed
     unsigned cyc_top;  // SM cycles spent in the reconstruction cuts (heavy_cut)
@@ -630,6 +631,7 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
     out.f = -1;
     out.reco = make_float4(0.f, 0.f, 0.f, 0.f);
     out.bin = 0;
+    out.score = 0.0f;
     out.evald = out.passd = out.cyc_top = out.cyc_met = out.cands = 0;
     float s[N > 0 ? N : 1];
 #pragma unroll
@@ -761,6 +763,7 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
             if (!met_done) met = sqrtf(fmaf(mx, mx, __fmul_rn(my, my)));
             out.bin = hist_bin_d(P, ff.mtop_had);
             out.reco = make_float4((float)ff.mtop_had, (float)ff.mtop_lep, (float)ff.pz, met);
+            out.score = (float)ff.chi2;
         }
     } else if (f == P.n_cuts) {
         // survivor: reconstructed quantities must be certain as well
@@ -776,6 +779,7 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         if (hu) return out;
         out.bin = bin;
         out.reco = make_float4(mt_b, mw_b, pz, met);
+        out.score = b1;
     }
     out.f = f;
     return out;

@@ -30,15 +30,17 @@ struct DlSmem {
     uint32_t* nj;    // [ev] jets
     uint32_t* btag;  // [ev]
     float4* ureco;   // [unit]
+    float2* usc;     // [unit] fit score and (bits of) bin, best-of-variations only
     int* uf;         // [unit]
 };
 
-__device__ inline DlSmem dl_carve(char* p, int ev, int units)
+__device__ inline DlSmem dl_carve(char* p, int ev, int units, bool best)
 {
     DlSmem t;
     t.jets = (float4*)p; p += (size_t)ev * 12 * 16;
     t.lep = (float4*)p; p += (size_t)ev * 32;
     t.ureco = (float4*)p; p += (size_t)units * 16;
+    t.usc = (float2*)p; p += best ? (size_t)units * 8 : 0;
     t.met = (float2*)p; p += (size_t)ev * 8;
     t.evid = (uint32_t*)p; p += (size_t)ev * 4;
     t.bits = (uint32_t*)p; p += (size_t)ev * 4;
@@ -48,7 +50,9 @@ __device__ inline DlSmem dl_carve(char* p, int ev, int units)
     return t;
 }
 
-// One tile: ne events (ents) of one chunk with all their variations.
+// One tile: ne events (ents) of one chunk with all their variations
+// (B: best-of-variations per event, else the means).
+template <bool B>
 __device__ void dilep_tile(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
                            uint64_t first_id, const uint2* ents, int ne, const DlSmem& sm, const int* exec,
                            int nexec, S2Acc& acc)
@@ -82,20 +86,21 @@ __device__ void dilep_tile(const Plan& P, const Cols& C, const Out& O, const Scr
                                  first_id + sm.evid[ev], v, seed);
         sm.uf[u] = r.f;
         sm.ureco[u] = r.reco;
-        warp_tally(P, r, acc.fc, acc.hist, &acc.st);
+        if constexpr (B) sm.usc[u] = make_float2(r.score, __int_as_float(r.bin));
+        warp_tally<B>(P, r, acc.fc, acc.hist, &acc.st);
     }
     __syncthreads();
     // C: per-event reduction
-    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, acc.fc, acc.hist,
+    reduce_tile_events<B>(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, sm.usc, acc.fc, acc.hist,
                        threadIdx.x, blockDim.x);
     __syncthreads();
 }
 
 }  // namespace
 
-size_t dl_smem_bytes(int ev, int units)
+size_t dl_smem_bytes(int ev, int units, bool best)
 {
-    return (size_t)ev * (12 * 16 + 32 + 8 + 16) + (size_t)units * 20 + 64;
+    return (size_t)ev * (12 * 16 + 32 + 8 + 16) + (size_t)units * (best ? 28 : 20) + 64;
 }
 
 int dl_ev_per_tile(uint32_t V, int upt)
@@ -104,6 +109,7 @@ int dl_ev_per_tile(uint32_t V, int upt)
     return e < 1 ? 1 : (e > 64 ? 64 : e);
 }
 
+template <bool B>
 __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols C, const Out O, Scratch S, uint32_t V,
                                                         uint64_t seed, uint64_t first_id, int ept)
 {
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols
     }
     acc.zero();
     __syncthreads();
-    DlSmem sm = dl_carve(smem_raw, ept, ept * (int)V);
+    DlSmem sm = dl_carve(smem_raw, ept, ept * (int)V, B);
     bool any = false;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(S.tile_ctr, 1u);
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(BLOCK) k_stage2_dilep(const Plan P, const Cols
         while (b > 0 && tile >= s_tiles[b - 1]) --b;
         const unsigned first = (tile - s_tiles[b]) * (unsigned)ept;
         const int ne = (int)min((unsigned)ept, s_fill[b] - first);
-        dilep_tile(P, C, O, S, V, seed, first_id, S.bucket + s_base[b] + first, ne, sm, s_exec, s_nexec, acc);
+        dilep_tile<B>(P, C, O, S, V, seed, first_id, S.bucket + s_base[b] + first, ne, sm, s_exec, s_nexec, acc);
     }
     if (!any) return;
     acc.flush(P, O, S.stats);
@@ -221,8 +227,8 @@ __global__ void __launch_bounds__(BLOCK) k_bstage2_dilep(const BatchDev* __restr
         const int ne = (int)min(ept, ch.cnt[16 + b] - first);
         Scratch S = B.S;
         S.chunk = (uint32_t)c;
-        DlSmem sm = dl_carve(smem_raw, (int)ept, (int)(ept * ch.V));
-        dilep_tile(s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first, ne, sm,
+        DlSmem sm = dl_carve(smem_raw, (int)ept, (int)(ept * ch.V), false);
+        dilep_tile<false>(s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first, ne, sm,
                    s_exec, s_nexec, acc);
     }
     if (cur >= 0) {
@@ -245,13 +251,14 @@ cudaError_t launch_bs2_dilep(const BatchDev* B, size_t smem, int sms, cudaStream
 cudaError_t launch_s2_dilep(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V, uint64_t seed,
                             uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
-    const size_t smem = dl_smem_bytes(ept, ept * (int)V);
-    cudaError_t e = ensure_smem_attr((const void*)k_stage2_dilep);
+    const size_t smem = dl_smem_bytes(ept, ept * (int)V, P.best);
+    auto k = P.best ? k_stage2_dilep<true> : k_stage2_dilep<false>;
+    cudaError_t e = ensure_smem_attr((const void*)k);
     if (e != cudaSuccess) return e;
     int bs = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_dilep, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k, BLOCK, smem);
     if (bs < 1) bs = 1;
-    k_stage2_dilep<<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
+    k<<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
     return cudaGetLastError();
 }
 

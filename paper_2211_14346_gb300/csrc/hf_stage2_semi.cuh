@@ -34,8 +34,8 @@
 namespace hf {
 
 // (B) of a tile of a triplet-only analysis: B1 probe, B2 chi2 of the listed
-// units, B3 completion, per sub-batch of HT_UNITS units.
-template <int N, class Grp>
+// units, B3 completion, per sub-batch of HT_UNITS units (B: best-of-variations).
+template <int N, bool B, class Grp>
 __device__ void semi_units_split(const Grp& g, const Plan& P, const Scratch& S, uint32_t V, uint64_t seed,
                                  uint64_t first_id, int ne, TileSmem& sm, const int* exec, int nexec,
                                  unsigned long long* fc, unsigned* hist, CutStats* st)
@@ -79,7 +79,8 @@ __device__ void semi_units_split(const Grp& g, const Plan& P, const Scratch& S, 
             } else {
                 sm.uf[u] = r.f;
                 sm.ureco[u] = r.reco;
-                warp_tally(P, r, fc, hist, st);
+                if constexpr (B) sm.usc[u] = make_float2(r.score, __int_as_float(r.bin));
+                warp_tally<B>(P, r, fc, hist, st);
             }
         }
         g.sync();
@@ -113,14 +114,15 @@ __device__ void semi_units_split(const Grp& g, const Plan& P, const Scratch& S, 
                 UnitOut r = semi_unit_f<N, false, UNIT_RESUME>(P, exec, nexec, se, v, seed, &t);
                 sm.uf[u] = r.f;
                 sm.ureco[u] = r.reco;
-                warp_tally(P, r, fc, hist, st);
+                if constexpr (B) sm.usc[u] = make_float2(r.score, __int_as_float(r.bin));
+                warp_tally<B>(P, r, fc, hist, st);
             }
         }
         g.sync();
     }
 }
 
-template <int N, bool F, class Grp>
+template <int N, bool F, bool B, class Grp>
 __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                           uint64_t seed, uint64_t first_id, const uint2* ents, int ne, TileSmem& sm,
                           const int* exec, int nexec, unsigned long long* fc, unsigned* hist, CutStats* st)
@@ -181,7 +183,7 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
     }
     const int nu = ne * (int)V;
     if constexpr (!F && N >= 3) {
-        semi_units_split<N>(g, P, S, V, seed, first_id, ne, sm, exec, nexec, fc, hist, st);
+        semi_units_split<N, B>(g, P, S, V, seed, first_id, ne, sm, exec, nexec, fc, hist, st);
     } else {
     // B: units
     for (int u = r0; u < nu; u += gs) {
@@ -197,12 +199,14 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
         UnitOut r = semi_unit_f<N, F>(P, exec, nexec, se, v, seed);
         sm.uf[u] = r.f;
         sm.ureco[u] = r.reco;
-        warp_tally(P, r, fc, hist, st);
+        if constexpr (B) sm.usc[u] = make_float2(r.score, __int_as_float(r.bin));
+        warp_tally<B>(P, r, fc, hist, st);
     }
     }
     g.sync();
     // C: per-event reduction in variation order
-    reduce_tile_events(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, fc, hist, r0, gs);
+    reduce_tile_events<B>(P, C, O, S, V, seed, first_id, ne, sm.evid, sm.bits, sm.uf, sm.ureco, sm.usc, fc, hist, r0,
+                          gs);
     g.sync();
 }
 
@@ -249,8 +253,9 @@ struct S2Acc {
 // Single chunk: the block takes tiles of bucket N from its tile counter.  The
 // block-wide barriers between the phases of a tile keep the block's warps at
 // nearby code addresses of the (long, fully unrolled) unit evaluation, which
-// measured faster than independent per-warp tiles.
-template <int N, bool F>
+// measured faster than independent per-warp tiles.  B: best-of-variations
+// (a kernel of its own, so that the per-event means carry none of its code).
+template <int N, bool F, bool B>
 __global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_stage2_semi(const Plan P, const Cols C, const Out O, Scratch S,
                                                        uint32_t V, uint64_t seed, uint64_t first_id,
                                                        int ev_per_tile)
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_stage2_semi(cons
     __syncthreads();
     if (s_fill == 0) return;
     const unsigned ntiles = (s_fill + ev_per_tile - 1) / ev_per_tile;
-    TileSmem sm = carve(smem_raw, ev_per_tile, ev_per_tile * (int)V, gram_stride(N));
+    TileSmem sm = carve(smem_raw, ev_per_tile, ev_per_tile * (int)V, gram_stride(N), B);
     bool any = false;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&S.tile_ctr[N], 1u);
@@ -283,8 +288,8 @@ __global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_stage2_semi(cons
         any = true;
         unsigned first = tile * (unsigned)ev_per_tile;
         int ne = (int)min((unsigned)ev_per_tile, s_fill - first);
-        semi_tile<N, F>(BlockGroup(), P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec, s_nexec,
-                     acc.fc, acc.hist, &acc.st);
+        semi_tile<N, F, B>(BlockGroup(), P, C, O, S, V, seed, first_id, S.bucket + s_base + first, ne, sm, s_exec,
+                           s_nexec, acc.fc, acc.hist, &acc.st);
     }
     if (!any) return;
     acc.flush(P, O, S.stats);
@@ -373,9 +378,9 @@ __global__ void __launch_bounds__(BLOCK, s2_min_blocks(N, F)) k_bstage2_semi(con
         const int ne = (int)min(ept, fill - first);
         Scratch S = B.S;
         S.chunk = (uint32_t)c;
-        TileSmem sm = carve(smem_raw, (int)ept, (int)(ept * ch.V), gram_stride(N));
-        semi_tile<N, F>(BlockGroup(), s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id, B.bucket + ch.ev0 + base + first,
-                     ne, sm, s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
+        TileSmem sm = carve(smem_raw, (int)ept, (int)(ept * ch.V), gram_stride(N), false);
+        semi_tile<N, F, false>(BlockGroup(), s_plan, ch.C, ch.O, S, ch.V, ch.seed, ch.first_id,
+                               B.bucket + ch.ev0 + base + first, ne, sm, s_exec, s_nexec, acc.fc, acc.hist, &acc.st);
     }
     if (cur >= 0) {
         const BChunk& pc = B.ch[cur];
@@ -388,13 +393,14 @@ template <int N, bool F>
 cudaError_t launch_s2_semi(const Plan& P, const Cols& C, const Out& O, const Scratch& S, uint32_t V,
                            uint64_t seed, uint64_t first_id, int ept, int sms, cudaStream_t st)
 {
-    const size_t smem = semi_smem_bytes(N, F, ept, ept * (int)V);
-    cudaError_t e = ensure_smem_attr((const void*)k_stage2_semi<N, F>);
+    const size_t smem = semi_smem_bytes(N, F, ept, ept * (int)V, P.best);
+    auto k = P.best ? k_stage2_semi<N, F, true> : k_stage2_semi<N, F, false>;
+    cudaError_t e = ensure_smem_attr((const void*)k);
     if (e != cudaSuccess) return e;
     int bs = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stage2_semi<N, F>, BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k, BLOCK, smem);
     if (bs < 1) bs = 1;
-    k_stage2_semi<N, F><<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
+    k<<<sms * bs, BLOCK, smem, st>>>(P, C, O, S, V, seed, first_id, ept);
     return cudaGetLastError();
 }
 
