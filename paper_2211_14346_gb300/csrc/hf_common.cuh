@@ -1185,9 +1185,17 @@ struct TopSmem {
     unsigned* nh;        // listed units
 };
 
+// Multiplicities whose triplet-only tiles take the split evaluation (probe,
+// chi2 of the listed units, completion).  Below 9 jets the whole unit in one
+// thread with the fully unrolled candidate loop measured faster (per-launch
+// times of each multiplicity: the split gains from 9 jets on, where the
+// candidates outnumber the rest of the unit's work and pair pruning pays).
+__host__ __device__ constexpr bool semi_split(int n, bool full) { return !full && n >= 9; }
+
 __host__ __device__ constexpr size_t top_smem_bytes(int n)
 {
-    return n >= 3 ? (size_t)HT_UNITS * (sizeof(TopIn) + 4) + (size_t)(n * n + n) * HT_SLOTS * 4 + 128 : 0;
+    return semi_split(n, false) ? (size_t)HT_UNITS * (sizeof(TopIn) + 4) + (size_t)(n * n + n) * HT_SLOTS * 4 + 128
+                                : 0;
 }
 
 // Byte offset of the Gram-term columns (qs) in the chi2 step's region; the

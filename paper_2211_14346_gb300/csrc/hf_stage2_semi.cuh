@@ -11,7 +11,7 @@
 // variation order and writes the event's outputs, or registers its flagged
 // units for the FP64 recheck.
 //
-// (B) for triplet-only analyses (N >= 3) runs in sub-batches of HT_UNITS
+// (B) for triplet-only analyses with N >= 9 jets runs in sub-batches of HT_UNITS
 // units and three steps: (B1) one thread per unit smears the MET and runs
 // the cut state machine up to the point where the triplet chi2 is needed
 // (UNIT_PROBE); those units are compacted into a list by warp ballot and a
@@ -20,7 +20,7 @@
 // smeared Gram terms in its own shared-memory column and the W pairs pruned
 // (hadtop_pruned), so every lane of a warp works on a unit that needs it,
 // and (B3) the same thread completes that unit (UNIT_RESUME) right away.  Analyses with
-// the full Eq. 1 fit, and N < 3, evaluate each unit whole in its thread.
+// the full Eq. 1 fit, and N < 9, evaluate each unit whole in its thread.
 //
 // k_stage2_semi<N>: persistent grid over the tiles of one chunk.
 // k_bstage2_semi<N>: persistent grid over the tiles of every semileptonic
@@ -131,7 +131,7 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
     // A: stage lepton / MET, then the packed Gram matrices
     constexpr int NT = ntri(N);
     constexpr int GST = gram_stride(N);
-    if constexpr (!F && N >= 3) {
+    if constexpr (semi_split(N, F)) {
         // the jets of the tile's events are first copied into the chi2 step's
         // shared-memory region (free until then), every load independent of the
         // others, so that the Gram terms wait for one round of global loads
@@ -182,7 +182,7 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
     g.sync();
     }
     const int nu = ne * (int)V;
-    if constexpr (!F && N >= 3) {
+    if constexpr (semi_split(N, F)) {
         semi_units_split<N, B>(g, P, S, V, seed, first_id, ne, sm, exec, nexec, fc, hist, st);
     } else {
     // B: units
@@ -211,12 +211,12 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
 }
 
 // Blocks per SM the stage-2 kernels are compiled for (the register budget):
-// the shared memory of a triplet-only tile allows at most 2 blocks per SM
-// from 9 jets on and 3 at 7-8 jets (the smeared Gram terms of the chi2
-// step), so those get the registers of that occupancy.
+// the shared memory of a split triplet-only tile (the smeared Gram terms of
+// the chi2 step) allows at most 2 blocks per SM, so those get the registers
+// of that occupancy; the others 4 (3 with the full fit from 9 jets on).
 __host__ __device__ constexpr int s2_min_blocks(int n, bool full)
 {
-    return full ? (n >= 9 ? 3 : 4) : (n >= 9 ? 2 : n >= 7 ? 3 : 4);
+    return full ? (n >= 9 ? 3 : 4) : (semi_split(n, full) ? 2 : 4);
 }
 
 // Block-level accumulators of the stage-2 kernels (shared memory).
