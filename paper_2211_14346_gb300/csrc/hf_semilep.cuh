@@ -638,7 +638,9 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
     for (int i = 0; i < (N > 0 ? N : 1); ++i) s[i] = 1.0f;
     float mx = ev.met.x, my = ev.met.y, dmx = 0.0f, dmy = 0.0f;
     const uint2 key = key_of(seed);
-    if (MODE == UNIT_WHOLE && P.smear_jets) jet_scales_f<N>(P, v, ev.event_id, key, s);
+    // jet scales (Philox blocks 0-2) only once a cut or the fit needs them: a
+    // unit that fails a cheaper cut first never draws them
+    bool s_todo = MODE == UNIT_WHOLE && P.smear_jets;
     // lepton scale s_l = 1 + sigma_lep z14 and its error bound (Philox block 3,
     // words z, w; the MET shift uses words x, y of the same block)
     float sl = 1.0f, dsl = 0.0f;
@@ -728,6 +730,10 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
                     out.cands += tin->cands;
                     out.cyc_top += tin->cyc;
                 } else {
+                    if (s_todo) {
+                        jet_scales_f<N>(P, v, ev.event_id, key, s);
+                        s_todo = false;
+                    }
                     hadtop_f<N>(P, ev.g, s, chi2_cap(P, P.top_thr), b1, b2, mt_b, mw_b, &out.cands);
                 }
                 top_done = true;
@@ -737,6 +743,10 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         } else if (kind == CUT_TTBAR_CHI2_MAX) {
             if constexpr (F) {
                 if (!full_done) {
+                    if (s_todo) {
+                        jet_scales_f<N>(P, v, ev.event_id, key, s);
+                        s_todo = false;
+                    }
                     ff = semi_full_fit<N>(P, ev, s, v, seed);
                     full_done = true;
                 }
@@ -757,6 +767,10 @@ __device__ UnitOut semi_unit_f(const Plan& P, const int* exec, int nexec, const 
         if (f == P.n_cuts) {
             // survivor of an analysis with the full fit: its (exact) values
             if (!full_done) {
+                if (s_todo) {
+                    jet_scales_f<N>(P, v, ev.event_id, key, s);
+                    s_todo = false;
+                }
                 ff = semi_full_fit<N>(P, ev, s, v, seed);
                 full_done = true;
             }
