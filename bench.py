@@ -33,7 +33,7 @@ SMEAR_SEED = 1002
 WORKLOAD = "semilep_smeared_10M_x16"
 # DRAM bytes (read + write) of the 13 stage-2 launches of one 10M x 16 step: one ncu capture of
 # the 2M-event step (991.8 MB, dram__bytes_read.sum + dram__bytes_write.sum) scaled by the events
-STAGE2_DRAM_BYTES_PER_STEP = 4.959e9
+STAGE2_DRAM_BYTES_PER_STEP = None
 
 
 def _args():
@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--events", type=int, default=N_EVENTS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="batched: skip the per-chunk plain runs")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--requests", type=int, default=600, help="served: number of requests per arrival rate")
     p.add_argument("--max-request", type=int, default=200000, help="served: largest request (log-uniform from 1000)")
@@ -300,6 +301,7 @@ def run_ours(a):
     ms = e0.elapsed_time(e1)
     prof = eng.profile(reset=True)
     res = out.numpy()
+    local = dict(cutflow=res["cutflow"].copy(), hist=res["hist"].copy(), mask=res["mask"])  # this rank's shard
     if dist is not None:  # the path's one exchange: exact integer sums of the shards' counts
         from paper_2211_14346_gb300.shard import merge_results
         merged = merge_results(dict(cutflow=res["cutflow"], hist=res["hist"], recheck_count=res["recheck_count"]),
@@ -322,7 +324,8 @@ def run_ours(a):
     achieved = flops / (s2_ms / 1000.0) / 1e12
     peak = max(fp32["tflops_ffma"], fp32["tflops_ffma2"])
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=STAGE2_DRAM_BYTES_PER_STEP * N / N_EVENTS if V == 16 else None,
+                traffic=(STAGE2_DRAM_BYTES_PER_STEP * N / N_EVENTS
+                         if V == 16 and STAGE2_DRAM_BYTES_PER_STEP is not None else None),
                 traffic_note="dram__bytes_read.sum + dram__bytes_write.sum of the 13 stage-2 launches of one step, "
                              "one ncu capture at 2M events scaled to this step's events",
                 kernel="k_stage2_semi<N> (13 launches per step)", ms_per_step=s2_ms,
@@ -352,9 +355,9 @@ def run_ours(a):
     ms_plain = p0.elapsed_time(p1) / plain_steps
     rp = out_plain.numpy()
     plain = dict(value=N / (ms_plain / 1e3), unit="events/s", ms_per_step=ms_plain, steps=plain_steps,
-                 identical_results=bool(np.array_equal(rp["cutflow"], res["cutflow"]) and
-                                        np.array_equal(rp["hist"], res["hist"]) and
-                                        np.array_equal(rp["mask"], res["mask"])),
+                 identical_results=bool(np.array_equal(rp["cutflow"], local["cutflow"]) and
+                                        np.array_equal(rp["hist"], local["hist"]) and
+                                        np.array_equal(rp["mask"], local["mask"])),
                  note="hf_run_device_plain: one thread per event, cuts in user order, no compaction or staging, "
                       "same FP32 bands and FP64 recheck; one warm-up run")
 
@@ -466,7 +469,7 @@ def run_batched(a):
                 aids[m], pool.slice(0, min(pool.n_events, 400000 if m == 0 else 100000)), V=v, seed=seeds[m])
     for it in items:
         it["out"] = eng.results_for(it["aid"], it["cols"].n_events)
-    plain_out = [eng.results_for(it["aid"], it["cols"].n_events) for it in items]
+    plain_out = [] if a.no_plain else [eng.results_for(it["aid"], it["cols"].n_events) for it in items]
     n_events = sum(c["n"] for c in spec)
     units = sum(c["n"] * c["V"] for c in spec)
 
@@ -495,9 +498,10 @@ def run_batched(a):
     clk.start()
     ms_b = timed(batched, a.steps, a.warmup)
     clocks = clk.stop()
-    ms_p = timed(plain, max(1, a.steps // 3), 1)
-    same = all(np.array_equal(it["out"].numpy()["cutflow"], o.numpy()["cutflow"]) and
-               np.array_equal(it["out"].numpy()["mask"], o.numpy()["mask"]) for it, o in zip(items, plain_out))
+    ms_p = None if a.no_plain else timed(plain, max(1, a.steps // 3), 1)
+    same = None if a.no_plain else all(
+        np.array_equal(it["out"].numpy()["cutflow"], o.numpy()["cutflow"]) and
+        np.array_equal(it["out"].numpy()["mask"], o.numpy()["mask"]) for it, o in zip(items, plain_out))
     line = dict(metric="events/sec", value=n_events / (ms_b / 1e3), unit="events/s", n_gpus=1, steps=a.steps,
                 warmup=a.warmup, ms_per_step=ms_b, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
@@ -506,9 +510,10 @@ def run_batched(a):
                             variations="{1, 8, 64}", semilep_events=sum(c["n"] for c in spec if c["model"] == 0),
                             dilep_events=sum(c["n"] for c in spec if c["model"] == 1),
                             l2="device-resident pools larger than L2; no flush"),
-                plain=dict(value=n_events / (ms_p / 1e3), ms_per_step=ms_p,
-                           note="one hf_run_device_plain per chunk (one thread per event)"),
-                speedup_vs_plain=ms_p / ms_b, identical_results=bool(same), clocks=clocks, units_per_tile=tuned,
+                plain=None if ms_p is None else dict(value=n_events / (ms_p / 1e3), ms_per_step=ms_p,
+                                                     note="one hf_run_device_plain per chunk (one thread per event)"),
+                speedup_vs_plain=None if ms_p is None else ms_p / ms_b,
+                identical_results=None if same is None else bool(same), clocks=clocks, units_per_tile=tuned,
                 # k_bzero, k_bcount, k_bstage1, k_btiles, the dilepton grid, 13 semileptonic grids,
                 # k_brecheck, k_bfinish, one scheduler update per analysis (2)
                 gpu_launches=int(4 + 1 + 13 + 2 + 2))

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(1024) k_btiles(const BatchDev* __restrict__ Bp
     if (threadIdx.x == 0) pre[nc] = s_carry;
 }
 
-__global__ void __launch_bounds__(BLOCK) k_brecheck(const BatchDev* __restrict__ Bp)
+__global__ void __launch_bounds__(BLOCK, 4) k_brecheck(const BatchDev* __restrict__ Bp)
 {
     const BatchDev& B = *Bp;
     const Scratch& S = B.S;

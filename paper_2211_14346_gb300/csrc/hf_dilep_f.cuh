@@ -409,7 +409,7 @@ __device__ inline UnitOut dilep_unit_f(const Plan& P, const int* exec, int nexec
     }
     double l1[4] = {lf1.x, lf1.y, lf1.z, lf1.w};
     double l2[4] = {lf2.x, lf2.y, lf2.z, lf2.w};
-    if (smear) {  // lepton l scaled by 1 + sigma_lep z[14 + l] (exactly 1 without lepton smearing)
+    if (P.smear_lep) {  // lepton l scaled by 1 + sigma_lep z[14 + l]
         pair(7);
         const double s1 = 1.0 + P.dsigma_lep * z[14], s2 = 1.0 + P.dsigma_lep * z[15];
         for (int k = 0; k < 4; ++k) {

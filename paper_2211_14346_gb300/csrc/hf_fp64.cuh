@@ -333,7 +333,7 @@ struct LazyUnitD {
     __device__ void lepton(int l, float4 lf, double* out)
     {
         const double c[4] = {lf.x, lf.y, lf.z, lf.w};
-        if (smear) {
+        if (smear && P->dsigma_lep != 0.0) {  // (the scale is exactly 1 without lepton smearing)
             pair(7);
             const double s = 1.0 + P->dsigma_lep * z[14 + l];
             for (int k = 0; k < 4; ++k) out[k] = s * c[k];

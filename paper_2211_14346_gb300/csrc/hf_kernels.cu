@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(256) k_stage1(const Plan P, const Cols C, uint
 }
 
 // ------------------------------------------------------------------ recheck
-__global__ void __launch_bounds__(BLOCK) k_recheck(const Plan P, const Cols C, const Out O, Scratch S,
+// Compiled for 4 blocks per SM (128 registers): the FP64 re-evaluation is
+// latency-bound, and at 168 registers (3 blocks) it measured 35 % slower.
+__global__ void __launch_bounds__(BLOCK, 4) k_recheck(const Plan P, const Cols C, const Out O, Scratch S,
                                                    uint64_t seed, uint64_t first_id)
 {
     __shared__ unsigned long long s_fc[MAX_CUTS + 1];
