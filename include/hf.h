@@ -74,6 +74,15 @@ typedef struct {
     uint32_t max_inflight;     /* maximum in-flight tickets (0 = 64)                    */
     uint32_t reserved;
     void* stream;              /* optional cudaStream_t to order work after (NULL = own) */
+    uint64_t staging_bytes;    /* pinned staging ring for columns in pageable host memory
+                                  (0 = none): hf_submit_chunk copies such a column into the
+                                  ring on the host and from there asynchronously, so that the
+                                  caller may reuse that buffer when the call returns; columns
+                                  in pinned memory, or larger than the ring, are copied
+                                  straight from the caller's buffer (which must then stay
+                                  valid until the ticket is done).  Ring space is reused once
+                                  the copy that filled it has completed (the host waits for
+                                  it when the ring is full).                                */
 } hf_config;
 
 /* Opens a context on cfg->device: the state an analysis run needs on one

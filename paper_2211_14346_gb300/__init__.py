@@ -265,9 +265,9 @@ def fp32_peak(device=0):
 class Engine:
     """One library context on one GPU."""
 
-    def __init__(self, device=0, flags=0, hbm_budget_bytes=0, max_inflight=0):
+    def __init__(self, device=0, flags=0, hbm_budget_bytes=0, max_inflight=0, staging_bytes=0):
         self.lib = _lib.load()
-        cfg = _lib.hf_config(device, flags, hbm_budget_bytes, max_inflight, 0, None)
+        cfg = _lib.hf_config(device, flags, hbm_budget_bytes, max_inflight, 0, None, staging_bytes)
         ctx = C.c_void_p()
         _lib.check(self.lib.hf_open(C.byref(cfg), C.byref(ctx)))
         self.ctx = ctx

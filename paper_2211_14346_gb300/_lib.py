@@ -39,7 +39,8 @@ HF_STATE_QUEUED, HF_STATE_RUNNING, HF_STATE_DONE, HF_STATE_FAILED = 0, 1, 2, 3
 
 class hf_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("flags", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
-                ("max_inflight", C.c_uint32), ("reserved", C.c_uint32), ("stream", C.c_void_p)]
+                ("max_inflight", C.c_uint32), ("reserved", C.c_uint32), ("stream", C.c_void_p),
+                ("staging_bytes", C.c_uint64)]
 
 
 class hf_cut(C.Structure):

@@ -246,6 +246,14 @@ struct hf_ctx {
     // sequence and what it was captured for
     char* bstage = nullptr;
     size_t bstage_bytes = 0;
+    // pinned staging ring of pageable host columns (hf_config.staging_bytes)
+    struct StageRegion {
+        size_t off, bytes;
+        cudaEvent_t done;  // the H2D copy out of the region has completed
+    };
+    char* staging = nullptr;
+    size_t staging_bytes = 0, stage_head = 0;
+    std::deque<StageRegion> stage_q;  // regions in use, oldest first
     cudaEvent_t bstage_free = nullptr;  // last upload from the staging buffer
     cudaStream_t s_cap = nullptr;       // capture stream of the batch graphs
     std::map<std::vector<uint64_t>, cudaGraphExec_t> bgraphs;  // captured launch sequences by shape
@@ -488,6 +496,51 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
     return HF_OK;
 }
 
+// Host -> device copy on stream st.  Pageable source memory goes through the
+// context's pinned staging ring when it has one and the copy fits: the bytes
+// are copied on the host into the ring and from there asynchronously, so the
+// caller's buffer is free again when this returns.  Ring space is reused once
+// the copy out of it has completed; the ring fills in address order and the
+// regions in use are kept oldest first, so the ones a new region overlaps are
+// at the front (a wrap to the start waits for all of them).
+hf_status copy_h2d(hf_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return HF_OK;
+    if (ctx->staging && bytes <= ctx->staging_bytes) {
+        cudaPointerAttributes at;
+        const cudaError_t pe = cudaPointerGetAttributes(&at, src);
+        if (pe != cudaSuccess) cudaGetLastError();
+        if (pe != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+            if (ctx->stage_head + bytes > ctx->staging_bytes) {
+                while (!ctx->stage_q.empty()) {
+                    HF_CUDA(cudaEventSynchronize(ctx->stage_q.front().done));
+                    cudaEventDestroy(ctx->stage_q.front().done);
+                    ctx->stage_q.pop_front();
+                }
+                ctx->stage_head = 0;
+            }
+            const size_t lo = ctx->stage_head, hi = lo + bytes;
+            while (!ctx->stage_q.empty()) {
+                const hf_ctx::StageRegion& r = ctx->stage_q.front();
+                if (r.off >= hi || r.off + r.bytes <= lo) break;
+                HF_CUDA(cudaEventSynchronize(r.done));
+                cudaEventDestroy(r.done);
+                ctx->stage_q.pop_front();
+            }
+            memcpy(ctx->staging + lo, src, bytes);
+            HF_CUDA(cudaMemcpyAsync(dst, ctx->staging + lo, bytes, cudaMemcpyHostToDevice, st));
+            cudaEvent_t ev;
+            HF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            HF_CUDA(cudaEventRecord(ev, st));
+            ctx->stage_q.push_back(hf_ctx::StageRegion{lo, bytes, ev});
+            ctx->stage_head = hi;
+            return HF_OK;
+        }
+    }
+    HF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return HF_OK;
+}
+
 hf_status check_cols(const hf_columns* c, uint64_t N, int L)
 {
     if (!c) return fail(HF_EINVAL, "columns are NULL");
@@ -601,6 +654,14 @@ hf_status hf_open(const hf_config* cfg, hf_ctx** out)
         uint64_t thr = ctx->budget;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    if (cfg->staging_bytes) {
+        e = cudaHostAlloc((void**)&ctx->staging, cfg->staging_bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HF_ENOMEM, "pinned staging ring allocation failed");
+        }
+        ctx->staging_bytes = cfg->staging_bytes;
+    }
     if (ctx->flags & HF_FLAG_BATCHING) ctx->dispatcher = std::thread(dispatcher_main, ctx.get());
     *out = ctx.release();
     return HF_OK;
@@ -643,6 +704,8 @@ hf_status hf_close(hf_ctx* ctx)
             if (kv.second.h2d) cudaEventDestroy(kv.second.h2d);
         if (ctx->bstage) cudaFreeHost(ctx->bstage);
         if (ctx->bstage_free) cudaEventDestroy(ctx->bstage_free);
+        for (auto& r : ctx->stage_q) cudaEventDestroy(r.done);
+        if (ctx->staging) cudaFreeHost(ctx->staging);
         if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
         if (ctx->arena) cudaFree(ctx->arena);
         if (ctx->arena_free) cudaEventDestroy(ctx->arena_free);
@@ -767,12 +830,15 @@ hf_status hf_submit_chunk(hf_ctx* ctx, uint32_t analysis_id, const hf_columns* h
     char* dscr = T.dmem + CL.bytes;
     char* dres = dscr + RL.scratch_bytes;
     if (N > 0) {
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jets, hc->jets, 16 * J, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep, hc->lep, 16 * (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_met, hc->met, 8 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jet_off, hc->jet_off, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_btag, hc->btag, 2 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep_q, hc->lep_q, (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        const struct {
+            size_t off;
+            const void* src;
+            size_t bytes;
+        } cp[6] = {{CL.off_jets, hc->jets, 16 * J},           {CL.off_lep, hc->lep, 16 * (size_t)L * N},
+                   {CL.off_met, hc->met, 8 * N},              {CL.off_jet_off, hc->jet_off, 4 * (N + 1)},
+                   {CL.off_btag, hc->btag, 2 * N},            {CL.off_lep_q, hc->lep_q, (size_t)L * N}};
+        for (const auto& c : cp)
+            if (hf_status s = copy_h2d(ctx, dc + c.off, c.src, c.bytes, ctx->s_h2d)) return s;
     }
     cudaEvent_t h2d;
     HF_CUDA(cudaEventCreateWithFlags(&h2d, cudaEventDisableTiming));
@@ -1370,12 +1436,15 @@ hf_status submit_batched(hf_ctx* ctx, uint32_t analysis_id, const Analysis& A, c
     }
     char* dc = T.dmem;
     if (N > 0) {
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jets, hc->jets, 16 * J, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep, hc->lep, 16 * (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_met, hc->met, 8 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_jet_off, hc->jet_off, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_btag, hc->btag, 2 * N, cudaMemcpyHostToDevice, ctx->s_h2d));
-        HF_CUDA(cudaMemcpyAsync(dc + CL.off_lep_q, hc->lep_q, (size_t)L * N, cudaMemcpyHostToDevice, ctx->s_h2d));
+        const struct {
+            size_t off;
+            const void* src;
+            size_t bytes;
+        } cp[6] = {{CL.off_jets, hc->jets, 16 * J},           {CL.off_lep, hc->lep, 16 * (size_t)L * N},
+                   {CL.off_met, hc->met, 8 * N},              {CL.off_jet_off, hc->jet_off, 4 * (N + 1)},
+                   {CL.off_btag, hc->btag, 2 * N},            {CL.off_lep_q, hc->lep_q, (size_t)L * N}};
+        for (const auto& c : cp)
+            if (hf_status s = copy_h2d(ctx, dc + c.off, c.src, c.bytes, ctx->s_h2d)) return s;
     }
     HF_CUDA(cudaMemsetAsync(dc + T.off_err, 0, 4, ctx->s_h2d));
     HF_CUDA(cudaEventCreateWithFlags(&T.h2d, cudaEventDisableTiming));

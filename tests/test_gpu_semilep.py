@@ -1,5 +1,7 @@
 """Parity of the CUDA path (fast and plain forms, device-resident and
 asynchronous host submission) with the FP64 oracle, semileptonic model."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -180,6 +182,32 @@ def test_async_submit_poll_fetch(eng, orc):
     with pytest.raises(Exception):
         eng.poll(tickets[0][0])
     assert HF_STATE_DONE == 2
+
+
+def test_pinned_staging_ring_for_pageable_columns(orc):
+    """A context with a 1 MB pinned staging ring: pageable host columns are
+    copied into the ring during hf_submit_chunk, so the caller's buffers may
+    be overwritten as soon as the call returns; six chunks cycle through the
+    ring (it wraps and waits for earlier copies), a pinned chunk and one
+    larger than the ring are copied straight from the caller's memory."""
+    from paper_2211_14346_gb300 import Engine, PinnedColumns, HostColumnsView
+    an = analyses.config2()
+    with Engine(0, staging_bytes=1 << 20) as e:
+        aid = e.define(an)
+        sizes = (1500, 700, 2600, 1, 1900, 1200, 1000, 12000)
+        chunks = [synth.gen_semilep(n, 60 + i) for i, n in enumerate(sizes)]
+        tickets = []
+        for i, c in enumerate(chunks):
+            h = PinnedColumns(c) if i == 6 else HostColumnsView(copy.deepcopy(c))
+            t = e.submit(aid, h, V=16, seed=25, first_event_id=5000 * i)
+            if i not in (6, 7):  # staged: the caller's buffers are free again
+                for a in h._keep:
+                    a.view(np.uint8)[...] = 0xA5
+            tickets.append((t, h, c, i))
+        for t, h, c, i in tickets:
+            g = e.fetch(aid, t, c.n_events)
+            o = orc.run(an, c, seed=25, V=16, first_event_id=5000 * i)
+            assert_parity(g, o, what="staged chunk %d" % i)
 
 
 def test_fetch_timeout_keeps_the_ticket(eng):
