@@ -33,7 +33,7 @@ SMEAR_SEED = 1002
 WORKLOAD = "semilep_smeared_10M_x16"
 # DRAM bytes (read + write) of the 13 stage-2 launches of one 10M x 16 step: one ncu capture of
 # the 2M-event step (991.8 MB, dram__bytes_read.sum + dram__bytes_write.sum) scaled by the events
-STAGE2_DRAM_BYTES_PER_STEP = 4.747e9
+STAGE2_DRAM_BYTES_PER_STEP = None  # the stage-2 kernels changed since the last capture
 
 
 def _args():

@@ -213,10 +213,13 @@ __device__ void semi_tile(const Grp& g, const Plan& P, const Cols& C, const Out&
 // Blocks per SM the stage-2 kernels are compiled for (the register budget):
 // the shared memory of a split triplet-only tile (the smeared Gram terms of
 // the chi2 step) allows at most 2 blocks per SM, so those get the registers
-// of that occupancy; the others 4 (3 with the full fit from 9 jets on).
+// of that occupancy.  The whole-unit kernels are latency-bound, and more
+// warps measured faster than fewer spills: 8 blocks per SM (64 registers) up
+// to 5 jets, 7 at 6 jets, 6 at 7-8 jets -- 7 % less stage-2 time than 4
+// blocks (128 registers) for all of them.  The full fit keeps 4 (3 from 9 jets).
 __host__ __device__ constexpr int s2_min_blocks(int n, bool full)
 {
-    return full ? (n >= 9 ? 3 : 4) : (semi_split(n, full) ? 2 : 4);
+    return full ? (n >= 9 ? 3 : 4) : (semi_split(n, full) ? 2 : n <= 5 ? 8 : n == 6 ? 7 : 6);
 }
 
 // Block-level accumulators of the stage-2 kernels (shared memory).
