@@ -72,3 +72,35 @@ def test_product_path_has_no_oracle_dependency():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "hf_oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and the field
+    offsets of the C structure of the same name in include/hf.h (compiled
+    with the host C compiler), so that no field is misplaced across the ABI."""
+    import shutil
+    from paper_2211_14346_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [v for k, v in vars(_lib).items()
+               if k.startswith("hf_") and isinstance(v, type) and issubclass(v, C.Structure)]
+    assert len(structs) >= 10
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "hf.h"', "int main(void) {"]
+    for s in structs:
+        n = s.__name__
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (n, n))
+        for f in s._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (n, f[0], n, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for s in structs:
+        n = s.__name__
+        assert int(got[n]) == C.sizeof(s), (n, got[n], C.sizeof(s))
+        for f in s._fields_:
+            assert int(got["%s.%s" % (n, f[0])]) == getattr(s, f[0]).offset, (n, f[0])
