@@ -253,7 +253,7 @@ struct hf_ctx {
     };
     char* staging = nullptr;
     size_t staging_bytes = 0, stage_head = 0;
-    std::deque<StageRegion> stage_q;  // regions in use, oldest first
+    std::deque<StageRegion> stage_q;  // regions in use, in address order below stage_head
     cudaEvent_t bstage_free = nullptr;  // last upload from the staging buffer
     cudaStream_t s_cap = nullptr;       // capture stream of the batch graphs
     std::map<std::vector<uint64_t>, cudaGraphExec_t> bgraphs;  // captured launch sequences by shape
@@ -499,10 +499,11 @@ hf_status enqueue_run(hf_ctx* ctx, Analysis& A, const Cols& C, uint64_t N, uint3
 // Host -> device copy on stream st.  Pageable source memory goes through the
 // context's pinned staging ring when it has one and the copy fits: the bytes
 // are copied on the host into the ring and from there asynchronously, so the
-// caller's buffer is free again when this returns.  Ring space is reused once
-// the copy out of it has completed; the ring fills in address order and the
-// regions in use are kept oldest first, so the ones a new region overlaps are
-// at the front (a wrap to the start waits for all of them).
+// caller's buffer is free again when this returns.  The ring fills in address
+// order; a copy that does not fit before its end starts again at the
+// beginning once every copy still in flight out of the ring has completed
+// (every region in use lies below the fill point, so nothing else can be
+// overwritten).
 hf_status copy_h2d(hf_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st)
 {
     if (!bytes) return HF_OK;
@@ -520,13 +521,6 @@ hf_status copy_h2d(hf_ctx* ctx, void* dst, const void* src, size_t bytes, cudaSt
                 ctx->stage_head = 0;
             }
             const size_t lo = ctx->stage_head, hi = lo + bytes;
-            while (!ctx->stage_q.empty()) {
-                const hf_ctx::StageRegion& r = ctx->stage_q.front();
-                if (r.off >= hi || r.off + r.bytes <= lo) break;
-                HF_CUDA(cudaEventSynchronize(r.done));
-                cudaEventDestroy(r.done);
-                ctx->stage_q.pop_front();
-            }
             memcpy(ctx->staging + lo, src, bytes);
             HF_CUDA(cudaMemcpyAsync(dst, ctx->staging + lo, bytes, cudaMemcpyHostToDevice, st));
             cudaEvent_t ev;
