@@ -168,7 +168,8 @@ typedef struct {
                                 histogram is filled once per selected event with that
                                 variation's value.  Device-resident single runs, the
                                 allocation-free run and unbatched submissions; not the plain
-                                form, hf_run_batch or HF_FLAG_BATCHING (HF_EINVAL)            */
+                                form, hf_run_batch, HF_FLAG_BATCHING or together with per-cut
+                                records (HF_EINVAL)                                           */
 
 /* Variables of the per-cut recording.  A variable is stored at every
  * recorded level; where it is not defined yet at that level it holds its
