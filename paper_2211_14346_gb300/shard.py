@@ -5,8 +5,8 @@ Events are independent and the smearing is keyed by the global event id
 contiguous event ranges, one per rank, gives per-event results that do not
 depend on the split.  The only exchange is at the end: integer sums of the
 cut flows, histograms and recheck counts, and the concatenation of the
-per-event outputs (mask, surviving variations, reconstructed means) in rank
-order.  Uses torch.distributed with whatever backend the process group has
+per-event outputs (mask, surviving variations, reconstructed quantities, the
+chosen variation of best-of-variations) in rank order.  Uses torch.distributed with whatever backend the process group has
 (NCCL between GPUs, gloo on CPU).
 """
 from __future__ import annotations
@@ -26,7 +26,7 @@ def merge_results(res: dict, group=None, device="cpu") -> dict:
     """Merges one rank's results (numpy arrays as returned by Engine.fetch or
     DeviceResults.numpy) with every other rank's.  Returns the merged dict on
     every rank: cutflow, hist and recheck_count summed exactly (int64), mask,
-    n_surv and reco concatenated in rank order."""
+    n_surv, reco and (best-of-variations) best_v concatenated in rank order."""
     import torch
     import torch.distributed as dist
     out = {}
@@ -46,7 +46,8 @@ def merge_results(res: dict, group=None, device="cpu") -> dict:
     dist.all_gather(all_sizes, sizes, group=group)
     all_sizes = [int(x.item()) for x in all_sizes]
     nmax = max(all_sizes) if all_sizes else 0
-    for k, dtype, width in (("mask", np.uint8, 1), ("n_surv", np.uint16, 1), ("reco", np.float32, 4)):
+    for k, dtype, width in (("mask", np.uint8, 1), ("n_surv", np.uint16, 1), ("reco", np.float32, 4),
+                            ("best_v", np.uint16, 1)):
         if k not in res:
             continue
         a = np.asarray(res[k], dtype=dtype).reshape(n_local, width)

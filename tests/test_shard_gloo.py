@@ -77,6 +77,57 @@ def test_shard_ranges_cover_exactly():
             assert max(h - l for l, h in rs) - min(h - l for l, h in rs) <= 1
 
 
+def _best_worker(rank, world, port, n, q):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+    import oracle
+    import synth as sy
+    from synth import analyses as an_mod
+    from paper_2211_14346_gb300.shard import shard_range, merge_results
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        cols = sy.gen_semilep(n, 31)
+        an = an_mod.semilep(sigma_jet=0.10, sigma_met=10.0)
+        lo, hi = shard_range(n, rank, world)
+        b = oracle.best_of(an, cols.slice(lo, hi), seed=8, V=6, first_event_id=lo)
+        r = dict(hist=b["hist"], reco=b["reco"].astype(np.float32), mask=(b["best_v"] >= 0).astype(np.uint8),
+                 best_v=np.where(b["best_v"] >= 0, b["best_v"], 0xffff).astype(np.uint16))
+        m = merge_results(r)
+        if rank == 0:
+            q.put({k: (v.tolist() if isinstance(v, np.ndarray) else v) for k, v in m.items()})
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_merge_of_best_of_variations(orc):
+    """Best-of-variations over two gloo ranks (the oracle on each shard): the
+    merged chosen variations, their quantities and the per-event histogram
+    equal the one-rank result."""
+    import multiprocessing as mp
+    n = 120
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_best_worker, args=(r, 2, port, n, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    m = q.get(timeout=180)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    an = analyses.semilep(sigma_jet=0.10, sigma_met=10.0)
+    b = orc.best_of(an, synth.gen_semilep(n, 31), seed=8, V=6)
+    want = np.where(b["best_v"] >= 0, b["best_v"], 0xffff).astype(np.uint16)
+    assert (want != 0xffff).sum() > 10
+    assert np.array_equal(np.asarray(m["best_v"], np.uint16), want)
+    assert np.array_equal(np.asarray(m["hist"], np.uint64), b["hist"])
+    assert np.array_equal(np.asarray(m["reco"], np.float32), b["reco"].astype(np.float32))
+
+
 def _gpu_worker(rank, world, port, n, q):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
