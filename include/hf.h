@@ -75,7 +75,9 @@ typedef struct {
     uint32_t reserved;
     void* stream;              /* optional cudaStream_t to order work after (NULL = own) */
     uint64_t staging_bytes;    /* pinned staging ring for columns in pageable host memory
-                                  (0 = none): hf_submit_chunk copies such a column into the
+                                  (0 = none; the input side of the overlap of reading and
+                                  processing that Sect. 5.1 gets from reader threads):
+                                  hf_submit_chunk copies such a column into the
                                   ring on the host and from there asynchronously, so that the
                                   caller may reuse that buffer when the call returns; columns
                                   in pinned memory, or larger than the ring, are copied
